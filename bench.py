@@ -1,0 +1,382 @@
+"""Benchmark: time-to-1e-10-residual of the mixed-precision even-odd CG solver
+on one GB300, against plain FP64 CG, with the hopping stencil's roofline.
+
+One step = one complete solve D x = b (FP64 true residual <= 1e-10 on all
+sites): link preparation is cached per gauge field, everything else (source
+preparation, the CG iterations with their reliable updates, reconstruction of
+the odd sites, the final FP64 residual) runs inside the step.  Inputs are
+resident in HBM when the timed region starts.  value = solves per second over
+all ranks.  Under torchrun every rank solves its own seeded system (weak
+scaling, no collective on the data path; a barrier brackets the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                  [--inner f16|bf16|f32|f64] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG time-to-1e-10 residual & Dslash GB/s (% HBM peak), mixed vs FP64 CG on GB300"
+DEFAULT_WORKLOAD = "wilson_32x32x32x64_exp0.6"
+# iteration count of plain FP64 CG on the normal equations over the full
+# lattice (the oracle's algorithm) for each seeded workload, used to scale the
+# oracle's per-iteration time to a time-to-solution
+ORACLE_CGNR_ITERS = {}
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2001_05218_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, kernel_name):
+    """DRAM bytes per launch of the stencil from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get(workload, {}).get(kernel_name)
+        if e and e.get("source_hash") == source_hash():
+            return e.get("dram_bytes_per_launch_full")
+    except Exception:
+        return None
+    return None
+
+
+# ---------------------------------------------------------------------- reference arm (the CPU oracle)
+def oracle_iteration_seconds(dims, kappa, U, b, reps):
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        w = O.dirac(dims, kappa, U, b)
+        O.dirac(dims, kappa, U, w, dag=True)
+    return (time.perf_counter() - t0) / reps
+
+
+def cpu_baseline(workload, dims, kappa, U, b, iters_needed, budget_s=20.0):
+    from oracle import oracle as O
+    O.build()
+    t1 = oracle_iteration_seconds(dims, kappa, U, b, 1)
+    reps = max(1, min(20, int(budget_s / max(t1, 1e-3))))
+    t = oracle_iteration_seconds(dims, kappa, U, b, reps)
+    solve_s = t * iters_needed
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d+1 CGNR iterations (D then D^dag, FP64, full lattice %s) of the oracle, %.3f s each, "
+                      "scaled by the %d iterations plain FP64 CGNR needs on this system" %
+                      (reps, "x".join(map(str, dims)), t, iters_needed)}
+
+
+def run_reference(args):
+    rank, world, _ = rank_info()
+    if rank != 0:
+        return
+    from paper_2001_05218_gb300 import inputs as I
+    from oracle import oracle as O
+    O.build()
+    dims, kappa, U, b = I.make_workload(args.workload)
+    iters = ORACLE_CGNR_ITERS.get(args.workload)
+    if iters is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no recorded oracle iteration count for %s"
+                          % args.workload}))
+        return
+    for _ in range(args.warmup):
+        oracle_iteration_seconds(dims, kappa, U, b, 1)
+    ts = []
+    for _ in range(args.steps):
+        ts.append(oracle_iteration_seconds(dims, kappa, U, b, 1))
+    t = float(np.mean(ts))
+    value = 1.0 / (t * iters)
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * iters * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded)", "impl": "reference",
+            "config": {"workload": args.workload, "lattice": list(dims), "kappa": kappa},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": "each step: one CGNR iteration (D then D^dag, FP64, full lattice) of the "
+                                       "oracle (%.3f s mean), scaled by the %d iterations plain FP64 CGNR needs"
+                                       % (t, iters)},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------- our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--inner", default=None)
+    ap.add_argument("--compress12", type=int, default=None)
+    ap.add_argument("--impl", default="ours")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = rank_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2001_05218_gb300 import dw
+    from paper_2001_05218_gb300 import inputs as I
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    wl = args.workload
+    big = I.WORKLOADS[wl]["dims"][3] >= 64
+    inner = args.inner or ("f16" if big else "f32")
+    c12 = args.compress12 if args.compress12 is not None else (1 if inner in ("f16", "bf16") else 0)
+    dims, kappa, U, b = I.make_workload(wl)
+    if rank > 0:  # independent system per rank: a different seeded source
+        b = I.gaussian_spinor(dims, I.workload_seed(I.WORKLOADS[wl]["index"]) + 1000 * rank, I.STREAM_SOURCE)
+    V = int(np.prod(dims))
+    Ug = dw.gauge(dims, kappa, U)
+    bg = dw.spinor(dims, b)
+    xg = dw.spinor(dims)
+    p_mix = dw.params(tol=1e-10, inner=inner, compress12=c12, maxiter=40000)
+    p_64 = dw.params(tol=1e-10, inner="f64", maxiter=40000)
+    zero = torch.zeros(xg.nbytes, dtype=torch.uint8, device="cuda")
+    l2_bytes = torch.cuda.get_device_properties(0).L2_cache_size
+    working_set = Ug.nbytes + bg.nbytes + xg.nbytes
+    flush = working_set < 4 * l2_bytes
+    scratch = torch.empty(2 * l2_bytes, dtype=torch.uint8, device="cuda") if flush else None
+
+    def reset_x():
+        xg.storage[xg.offset:xg.offset + xg.nbytes].copy_(zero)
+
+    def solve(p):
+        reset_x()
+        if flush:
+            scratch.fill_(1)
+        return dw.cg_solve(Ug, bg, xg, p)
+
+    for _ in range(max(3, args.warmup)):
+        solve(p_mix)
+    barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    dw.profile_start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    stats = []
+    for k in range(args.steps):
+        reset_x()
+        if flush:
+            scratch.fill_(1)
+        ev[k][0].record(stream)
+        s, st = dw.cg_solve(Ug, bg, xg, p_mix)
+        ev[k][1].record(stream)
+        stats.append(st[0])
+    t1.record(stream)
+    barrier()
+    prof, launches = dw.profile_stop()
+    clocks = clk.stop()
+    total_ms = t0.elapsed_time(t1)
+    step_ms = [a.elapsed_time(b_) for a, b_ in ev]
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    solve_ms = float(np.mean(step_ms))
+    value = world * args.steps / (total_ms / 1e3)
+    x_host = xg.download()
+    st0 = stats[-1]
+
+    # dominant kernel: the stencil category with the largest summed time
+    dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
+    per_launch_ms = dom["total_ms"] / dom["launches"]
+    per_launch_bytes = dom["bytes"] / dom["launches"]
+    achieved = per_launch_bytes / (per_launch_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    hop_total_ms = sum(v["total_ms"] for v in prof.values())
+
+    # FP64 CG on the same system, same GPU
+    fp64 = None
+    if not args.no_fp64:
+        solve(p_64)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        dw.profile_start()
+        reset_x()
+        e0.record(stream)
+        s64, st64 = dw.cg_solve(Ug, bg, xg, p_64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        prof64, _ = dw.profile_stop()
+        d64 = prof64.get("hop f64/f64", None)
+        fp64 = {"ms": e0.elapsed_time(e1), "iters": st64[0]["iters"], "true_rel_resid": st64[0]["true_rel_resid"]}
+        if d64:
+            pl = d64["total_ms"] / d64["launches"]
+            fp64["hop_f64"] = {"achieved_gbs": d64["bytes"] / d64["launches"] / (pl / 1e3) / 1e9,
+                               "achieved_tflops": d64["flops"] / d64["launches"] / (pl / 1e3) / 1e12,
+                               "ms_per_launch": pl, "frac_hbm": d64["bytes"] / d64["launches"] / (pl / 1e3) / 1e9 / peak}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        Uh = torch.from_numpy(U.reshape(-1).view(np.float64)).pin_memory()
+        bh = torch.from_numpy(b.reshape(-1).view(np.float64)).pin_memory()
+        xh = torch.empty(bh.numel(), dtype=torch.float64).pin_memory()
+        sp = dw.current_stream()
+
+        def e2e_step():
+            dw.check(dw.dw_field_upload(Ug.handle, ctypes.c_void_p(Uh.data_ptr()), sp))
+            dw.check(dw.dw_field_upload(bg.handle, ctypes.c_void_p(bh.data_ptr()), sp))
+            reset_x()
+            dw.cg_solve(Ug, bg, xg, p_mix)
+            dw.check(dw.dw_field_download(xg.handle, ctypes.c_void_p(xh.data_ptr()), sp))
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step()
+        barrier()
+        a0 = time.perf_counter()
+        ne = max(2, args.steps // 2)
+        for _ in range(ne):
+            e2e_step()
+        barrier()
+        e2e_s = (time.perf_counter() - a0) / ne
+        e2e = {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(Uh.numel() * 8 + bh.numel() * 8),
+               "d2h_bytes_per_step": int(xh.numel() * 8), "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        iters = ORACLE_CGNR_ITERS.get(wl)
+        how = "recorded"
+        if iters is None:
+            # same recurrence as the oracle (CGNR, full lattice) measured here
+            xf = dw.spinor(dims)
+            _, stf = dw.cg_solve(Ug, bg, xf, dw.params(tol=1e-10, inner="f32", eo=0, maxiter=100000))
+            iters = stf[0]["iters"]
+            how = "measured with the full-lattice CGNR of this library (FP32 inner, FP64 reliable updates)"
+        cpu = cpu_baseline(wl, dims, kappa, U, b, iters)
+        cpu["iters_source"] = how
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": solve_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "%s-storage/fp32-arith inner, f64 reliable" % inner if inner != "f64" else "f64",
+        "data": "synthetic (seeded exp(i a H) links, Gaussian source)",
+        "config": {"workload": wl, "lattice": list(dims), "kappa": kappa, "solver": "even-odd CGNR",
+                   "inner": inner, "compress12": c12, "tol": 1e-10, "global_batch": world, "parallelism": "replicas",
+                   "l2": "flushed between steps" if flush else "inputs larger than L2 (%d MB working set)" %
+                         (working_set >> 20)},
+        "mixed_cg": {"ms": solve_ms, "iters": st0["iters"], "reliable_updates": st0["reliable_updates"],
+                     "true_rel_resid": st0["true_rel_resid"], "normal_rel_resid": st0["normal_rel_resid"],
+                     "stencil_ms_share": hop_total_ms / sum(step_ms)},
+        "fp64_cg": fp64,
+        "speedup_vs_fp64": (fp64["ms"] / solve_ms) if fp64 else None,
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": ncu_traffic(wl, dom_name), "bytes_per_launch": per_launch_bytes,
+                     "ms_per_launch": per_launch_ms, "launches": dom["launches"],
+                     "gflops": dom["flops"] / dom["launches"] / (per_launch_ms / 1e3) / 1e9},
+        "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in prof.items()},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * dw.h -- C ABI of the GB300 (sm_103a) Wilson-Dirac conjugate-gradient library.
+ *
+ * The problem (Korcyl & Korcyl, SoftwareX, Sec. 1 and Sec. 3.3): solve the
+ * large sparse linear system whose matrix is the Dirac-Wilson operator by
+ * conjugate gradient, with most of the work in a low-precision data type and
+ * occasional high-precision corrections (Sec. 2).  The operator, on an
+ * Lx*Ly*Lz*Lt lattice with 12 complex components per site (4 spins x 3
+ * colours) and one 3x3 complex link matrix per site and direction (Fig. 1
+ * caption), is
+ *
+ *   D(x,y) = delta_xy - kappa * sum_mu [ (1 - gamma_mu) U_mu(x) delta_{x+mu,y}
+ *                                      + (1 + gamma_mu) U_mu(x-mu)^dag delta_{x-mu,y} ]
+ *
+ * = 1 - kappa*H with the hopping term H.  Space is periodic; time is
+ * antiperiodic when t_antiperiodic != 0 (sign -1 on links crossing
+ * t = Lt-1 -> 0).  gamma basis: chiral, gamma_k = [[0, -i sigma_k],
+ * [i sigma_k, 0]] (k = 1,2,3 for mu = x,y,z), gamma_t = [[0,1],[1,0]],
+ * gamma_5 = diag(1,1,-1,-1).
+ *
+ * Even-odd split: sites have parity (x+y+z+t) mod 2.  With H_eo (odd -> even)
+ * and H_oe, the Schur complement on even sites is
+ *   Dhat = 1 - kappa^2 H_eo H_oe,   Dhat^dag = gamma_5 Dhat gamma_5.
+ *
+ * Conventions for every call
+ *   - All device work is enqueued on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream) and is asynchronous, except the solvers, which
+ *     synchronise `stream` before returning so that they can fill statistics.
+ *   - Inputs are never modified.  On DW_ERR_ARG / DW_ERR_SHAPE /
+ *     DW_ERR_PRECISION nothing is enqueued and outputs are untouched.
+ *   - The library owns the memory of fields made by dw_field_alloc; memory
+ *     handed to dw_field_wrap stays owned by the caller and must outlive the
+ *     field handle.
+ *   - dw_last_error() returns a thread-local message for the last failure.
+ *   - Dimensions must all be even and Lx*Ly*Lz*Lt/2 must be a multiple of 8.
+ *
+ * Host canonical layout (complex128 as interleaved re, im doubles):
+ *   site s = x + Lx*(y + Ly*(z + Lz*t))
+ *   gauge         U[s][mu][row][col]                 (V*4*9 complex)
+ *   full spinor   psi[rhs][s][spin][colour]          (nrhs*V*12 complex)
+ *   parity spinor psi[rhs][j][spin][colour], j = the sites of that parity in
+ *                 increasing s order, i.e. j = s/2  (nrhs*V/2*12 complex)
+ */
+#ifndef DW_H
+#define DW_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t, declared without the CUDA headers. */
+typedef struct CUstream_st* dw_stream_t;
+
+typedef enum {
+  DW_OK = 0,
+  DW_ERR_ARG = 1,           /* NULL pointer, bad enum, bad parameter value */
+  DW_ERR_SHAPE = 2,         /* lattice / kind / nrhs mismatch between fields */
+  DW_ERR_PRECISION = 3,     /* unsupported or mismatched storage precision */
+  DW_ERR_OOM = 4,           /* device allocation failed */
+  DW_ERR_CUDA = 5,          /* a CUDA runtime call failed (message in dw_last_error) */
+  DW_ERR_NOT_CONVERGED = 6, /* maxiter reached; x holds the last FP64 iterate */
+  DW_ERR_BREAKDOWN = 7,     /* CG breakdown (p^dag A p <= 0 or not finite) */
+  DW_ERR_TIMEOUT = 8        /* device-side wall-time budget exhausted */
+} dw_status;
+
+typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3 } dw_prec;
+
+typedef enum {
+  DW_GAUGE = 0,       /* links U_mu(x), all sites */
+  DW_SPINOR_FULL = 1, /* spinor on all sites */
+  DW_SPINOR_EVEN = 2, /* spinor on even sites only */
+  DW_SPINOR_ODD = 3   /* spinor on odd sites only */
+} dw_kind;
+
+typedef struct {
+  int dims[4];        /* Lx, Ly, Lz, Lt (all even) */
+  int t_antiperiodic; /* 1: antiperiodic in time, 0: periodic */
+  double kappa;       /* hopping parameter (read from the gauge field's lattice) */
+} dw_lattice;
+
+typedef struct dw_field dw_field; /* opaque handle */
+
+/* ------------------------------------------------------------------ fields */
+
+/* Device bytes a field of this shape occupies (for dw_field_wrap).
+ * 16-bit spinors store 24 halves plus one FP32 scale per site; 16-bit links
+ * store the link entries directly (|U_ij| <= 1).  compress12 applies to
+ * gauge fields: only rows 0 and 1 are stored and row 2 is rebuilt as
+ * conj(row0 x row1), valid for SU(3) links. */
+dw_status dw_field_bytes(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs,
+                         size_t* bytes);
+
+/* Allocate a field in device memory (owned by the library, freed by dw_field_free). */
+dw_status dw_field_alloc(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs,
+                         dw_field** out);
+
+/* Make a field handle over caller-owned device memory of at least
+ * dw_field_bytes() bytes, 256-byte aligned (e.g. a torch tensor's storage). */
+dw_status dw_field_wrap(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs,
+                        void* dev_ptr, size_t bytes, dw_field** out);
+
+/* Release a handle (and its memory if it was made by dw_field_alloc).
+ * Waits for the device to finish work that may use it. */
+dw_status dw_field_free(dw_field* f);
+
+/* Copy host canonical complex128 data into the field (converted to the
+ * field's storage precision and layout).  `host` may be pageable or pinned;
+ * with pinned memory the copy is asynchronous on `stream` and the host buffer
+ * must stay valid until the stream reaches this point. */
+dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream);
+
+/* Copy the field back to host canonical complex128.  Data are valid once
+ * `stream` has been synchronised. */
+dw_status dw_field_download(const dw_field* f, double* host, dw_stream_t stream);
+
+/* As upload/download, with the canonical complex128 array in device memory. */
+dw_status dw_field_import(dw_field* f, const double* dev_canonical, dw_stream_t stream);
+dw_status dw_field_export(const dw_field* f, double* dev_canonical, dw_stream_t stream);
+
+/* Shape of a field. Any output pointer may be NULL. */
+dw_status dw_field_info(const dw_field* f, dw_lattice* lat, dw_kind* kind, dw_prec* prec, int* compress12,
+                        int* nrhs);
+
+/* --------------------------------------------------------------- operators */
+
+/* out = D in.  in/out FULL: the operator on all sites.  in/out EVEN (ODD):
+ * the Schur complement on that parity, 1 - kappa^2 H_pq H_qp.  U, in and out
+ * share one storage precision (FP64: IEEE binary64 throughout; FP32: binary32;
+ * FP16/BF16: 16-bit storage with FP32 arithmetic).  kappa and the boundary
+ * condition come from U's lattice.  in and out must not alias. */
+dw_status dw_apply(const dw_field* U, const dw_field* in, dw_field* out, dw_stream_t stream);
+
+/* out = D^dag in (same rules as dw_apply). */
+dw_status dw_apply_dag(const dw_field* U, const dw_field* in, dw_field* out, dw_stream_t stream);
+
+/* out = D^dag D in, or Dhat^dag Dhat in for parity fields. */
+dw_status dw_normal_apply(const dw_field* U, const dw_field* in, dw_field* out, dw_stream_t stream);
+
+/* ------------------------------------------------------------------ solvers */
+
+typedef struct {
+  double tol;          /* stop when |b - D x| / |b| <= tol, recomputed in FP64 */
+  int maxiter;         /* CG iteration limit */
+  dw_prec inner;       /* DW_F64: plain FP64 CG.  DW_F32/F16/BF16: mixed-precision
+                          CG with FP64 reliable updates */
+  double delta;        /* reliable update when |r| < delta * |r at last update| */
+  int eo;              /* 1: even-odd preconditioned (Schur system on even sites) */
+  int compress12;      /* inner-precision links stored as 12 reals */
+  int recompute_fwd;   /* dw_cg_backward: 1 = recompute the forward solution */
+  int tile;            /* sites per thread block (0 = library choice) */
+  int check_every;     /* iterations per convergence poll (0 = library choice) */
+  double timeout_s;    /* device-side time budget per solve (0 = none) */
+} dw_solver_params;
+
+typedef struct {
+  int iters;              /* CG iterations */
+  int reliable_updates;   /* FP64 residual replacements */
+  double true_rel_resid;  /* |b - D x| / |b| recomputed in FP64 on all sites */
+  double normal_rel_resid;/* |D^dag (b - D x)| / |D^dag b| (FP64) */
+  double time_ms;         /* wall time of the solve on the stream */
+  double flops;           /* model flop count (1320 per site per hop) */
+  double bytes;           /* model HBM bytes */
+  int status;             /* dw_status of this system */
+} dw_solver_stats;
+
+/* Fill *p with defaults: tol 1e-10, maxiter 20000, inner DW_F32, delta 0.1,
+ * eo 1, compress12 0, recompute_fwd 1, tile 0, check_every 0, timeout 0. */
+dw_status dw_solver_params_default(dw_solver_params* p);
+
+/* Solve D x = b by CG on the normal equations D^dag D x = D^dag b (with the
+ * even-odd Schur system when p->eo).  U: FP64 gauge field (18 reals).  b, x:
+ * FP64 FULL spinors of equal nrhs; every right-hand side is solved.  x holds
+ * the initial guess on entry.  stats: one entry per right-hand side (may be
+ * NULL).  Returns the worst status over right-hand sides. */
+dw_status dw_cg_solve(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
+                      dw_solver_stats* stats, dw_stream_t stream);
+
+/* n independent systems (lattices of any sizes, each with its own gauge
+ * field and kappa) solved together: every kernel launch of the iteration
+ * covers all systems.  All b[i] must have the same nrhs.  stats: n*nrhs
+ * entries, system-major (may be NULL). */
+dw_status dw_cg_solve_batched(int n, const dw_field* const* U, const dw_field* const* b, dw_field* const* x,
+                              const dw_solver_params* p, dw_solver_stats* stats, dw_stream_t stream);
+
+/* x = (D^dag D)^{-1} b by plain CG on the normal operator (rhs b itself), all
+ * sites; used for differentiation.  Same argument rules as dw_cg_solve. */
+dw_status dw_cg_solve_normal(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
+                             dw_solver_stats* stats, dw_stream_t stream);
+
+/* Gradients of the two differentiable forms (PyTorch convention for complex
+ * numbers: for a real loss L, grad z = dL/dRe z + i dL/dIm z).
+ *   grad_x != NULL:  forward x = (D^dag D)^{-1} b, incoming grad_x = dL/dx.
+ *                    grad_b = (D^dag D)^{-1} grad_x (a second CG solve);
+ *                    grad_U = F(D x, grad_b) + F(D grad_b, x).
+ *   grad_x == NULL:  S = phi^dag (D^dag D)^{-1} phi with phi = phi_or_b.
+ *                    grad_b = dS/dphi = 2 X, X = (D^dag D)^{-1} phi;
+ *                    grad_U = 2 F(D X, X).
+ * F(Y, X)_mu(x) = kappa eta_mu(x) sum_s [ w_s X(x+mu)_s^dag + X(x)_s w'_s^dag ],
+ * w = (1 - gamma_mu) Y(x), w' = (1 + gamma_mu) Y(x+mu) (eta = boundary sign).
+ * su3_project != 0 replaces grad_U by its su(3) projection P(G U^dag),
+ * P(M) = (M - M^dag)/2 - tr(M - M^dag)/6, the derivative along U -> exp(eps T) U.
+ * x_fwd: the forward solution (x, or X for the action) or NULL to recompute it.
+ * grad_b: FP64 FULL spinor; grad_U: FP64 gauge field (18 reals). */
+dw_status dw_cg_backward(const dw_field* U, const dw_field* phi_or_b, const dw_field* grad_x,
+                         const dw_field* x_fwd, dw_field* grad_b, dw_field* grad_U, int su3_project,
+                         const dw_solver_params* p, dw_solver_stats* stats, dw_stream_t stream);
+
+/* ----------------------------------------------------------- instrumentation */
+
+/* Launch accounting for measurement (no counterpart in the paper, whose
+ * Fig. 2 is a simulated timeline).  Between start and stop every kernel
+ * launch of the library is counted, and every stencil launch is bracketed by
+ * two CUDA events on its own stream.  Entries aggregate the stencil launches
+ * by (arithmetic precision / link storage): launches, summed event time,
+ * algorithmic bytes (links 8 per site once per site, each spinor touched
+ * once) and model flops (1320 per output site).  stop synchronises the
+ * device; while active it adds two event records per stencil launch. */
+typedef struct {
+  char name[64];
+  long long launches;
+  double total_ms;
+  double bytes;
+  double flops;
+} dw_profile_entry;
+
+dw_status dw_profile_start(void);
+dw_status dw_profile_stop(dw_profile_entry* entries, int max_entries, int* n_entries, long long* launches);
+
+/* ------------------------------------------------------------------- misc */
+
+const char* dw_last_error(void);
+
+/* Library version string. */
+const char* dw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DW_H */

@@ -1,0 +1,567 @@
+// dw_common.cuh -- device-side building blocks of the Wilson-Dirac CG library:
+// complex arithmetic, field storage formats, the batch/system descriptor and
+// the deterministic one-pass grid reduction with the CG scalar updates.
+//
+// Storage (per parity block of Vh sites, per right-hand side), structure of
+// arrays so that consecutive threads (consecutive even-odd site indices)
+// touch consecutive 16-byte words:
+//   spinor FP64 : 12 planes of double2       (complex k = 3*spin + colour)
+//   spinor FP32 :  6 planes of float4        (complex 2j, 2j+1)
+//   spinor F16/BF16: 3 planes of 8 halves (uint4) + 1 plane of FP32 per-site
+//                  scale; stored value = component / max|component of site|
+//   links  (parity p of the base site, direction mu) planes of
+//          FP64 18: 9 double2   FP64 12: 6 double2
+//          FP32 18: 9 float2    FP32 12: 3 float4
+//          F16/BF16 18: uint4, uint4, uint (18 halves)
+//          F16/BF16 12: uint4, uint2 (12 halves)
+//   12-real links keep rows 0 and 1; row 2 = conj(row0 x row1) (SU(3)).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dw {
+
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+
+// ------------------------------------------------------------------ complex
+template <typename R>
+struct Cx {
+  R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ Cx<R> cx(R a, R b) {
+  Cx<R> c;
+  c.re = a;
+  c.im = b;
+  return c;
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> operator+(Cx<R> a, Cx<R> b) { return cx(a.re + b.re, a.im + b.im); }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator-(Cx<R> a, Cx<R> b) { return cx(a.re - b.re, a.im - b.im); }
+template <typename R>
+__device__ __forceinline__ Cx<R> operator*(R s, Cx<R> a) { return cx(s * a.re, s * a.im); }
+// i*a
+template <typename R>
+__device__ __forceinline__ Cx<R> mul_i(Cx<R> a) { return cx(-a.im, a.re); }
+// a*b
+template <typename R>
+__device__ __forceinline__ Cx<R> cmul(Cx<R> a, Cx<R> b) {
+  return cx(fma(a.re, b.re, -a.im * b.im), fma(a.re, b.im, a.im * b.re));
+}
+// c + a*b
+template <typename R>
+__device__ __forceinline__ Cx<R> cmadd(Cx<R> a, Cx<R> b, Cx<R> c) {
+  return cx(fma(a.re, b.re, fma(-a.im, b.im, c.re)), fma(a.re, b.im, fma(a.im, b.re, c.im)));
+}
+// conj(a)*b
+template <typename R>
+__device__ __forceinline__ Cx<R> cjmul(Cx<R> a, Cx<R> b) {
+  return cx(fma(a.re, b.re, a.im * b.im), fma(a.re, b.im, -a.im * b.re));
+}
+// c + conj(a)*b
+template <typename R>
+__device__ __forceinline__ Cx<R> cjmadd(Cx<R> a, Cx<R> b, Cx<R> c) {
+  return cx(fma(a.re, b.re, fma(a.im, b.im, c.re)), fma(a.re, b.im, fma(-a.im, b.re, c.im)));
+}
+template <typename R>
+__device__ __forceinline__ Cx<R> conjx(Cx<R> a) { return cx(a.re, -a.im); }
+
+// ------------------------------------------------------------------ 16-bit helpers
+template <int P>
+struct H16;
+template <>
+struct H16<P16> {
+  __device__ static __forceinline__ float2 to2(uint32_t w) {
+    __half2 h = *reinterpret_cast<__half2*>(&w);
+    return __half22float2(h);
+  }
+  __device__ static __forceinline__ uint32_t from2(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+template <>
+struct H16<PB16> {
+  __device__ static __forceinline__ float2 to2(uint32_t w) {
+    __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+    return __bfloat1622float2(h);
+  }
+  __device__ static __forceinline__ uint32_t from2(float a, float b) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+
+// ------------------------------------------------------------------ spinor storage
+template <int P>
+struct Spin;
+
+template <>
+struct Spin<P64> {
+  using R = double;
+  static constexpr int kBytes = 192;  // bytes per site
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<double> (&v)[12]) {
+    const double2* b = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 t = __ldg(b + (size_t)k * vh + s);
+      v[k] = cx(t.x, t.y);
+    }
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<double> (&v)[12]) {
+    double2* b = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) b[(size_t)k * vh + s] = make_double2(v[k].re, v[k].im);
+  }
+  // v <- the value a store followed by a load would give
+  __device__ static __forceinline__ void roundtrip(Cx<double> (&)[12]) {}
+};
+
+template <>
+struct Spin<P32> {
+  using R = float;
+  static constexpr int kBytes = 96;
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&v)[12]) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      float4 t = __ldg(b + (size_t)k * vh + s);
+      v[2 * k] = cx(t.x, t.y);
+      v[2 * k + 1] = cx(t.z, t.w);
+    }
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&v)[12]) {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      b[(size_t)k * vh + s] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+  }
+  __device__ static __forceinline__ void roundtrip(Cx<float> (&)[12]) {}
+};
+
+template <int P>
+struct Spin16 {
+  using R = float;
+  static constexpr int kBytes = 52;  // 48 bytes of halves + 4 bytes of scale
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&v)[12]) {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+    const float sc = __ldg(reinterpret_cast<const float*>(base + (size_t)48 * vh) + s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 t = __ldg(b + (size_t)k * vh + s);
+      float2 a = H16<P>::to2(t.x), c = H16<P>::to2(t.y), d = H16<P>::to2(t.z), e = H16<P>::to2(t.w);
+      v[4 * k + 0] = cx(a.x * sc, a.y * sc);
+      v[4 * k + 1] = cx(c.x * sc, c.y * sc);
+      v[4 * k + 2] = cx(d.x * sc, d.y * sc);
+      v[4 * k + 3] = cx(e.x * sc, e.y * sc);
+    }
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&v)[12]) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+    uint4* b = reinterpret_cast<uint4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 t;
+      t.x = H16<P>::from2(v[4 * k + 0].re * inv, v[4 * k + 0].im * inv);
+      t.y = H16<P>::from2(v[4 * k + 1].re * inv, v[4 * k + 1].im * inv);
+      t.z = H16<P>::from2(v[4 * k + 2].re * inv, v[4 * k + 2].im * inv);
+      t.w = H16<P>::from2(v[4 * k + 3].re * inv, v[4 * k + 3].im * inv);
+      b[(size_t)k * vh + s] = t;
+    }
+    reinterpret_cast<float*>(base + (size_t)48 * vh)[s] = m;
+  }
+  __device__ static __forceinline__ void roundtrip(Cx<float> (&v)[12]) {
+    float m = 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+    const float inv = m > 0.f ? 1.0f / m : 0.f;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      float2 q = H16<P>::to2(H16<P>::from2(v[k].re * inv, v[k].im * inv));
+      v[k] = cx(q.x * m, q.y * m);
+    }
+  }
+};
+template <>
+struct Spin<P16> : Spin16<P16> {};
+template <>
+struct Spin<PB16> : Spin16<PB16> {};
+
+// ------------------------------------------------------------------ link storage
+template <typename R>
+__device__ __forceinline__ void rebuild_row2(Cx<R> (&u)[9]) {
+  // row2 = conj(row0 x row1)
+  u[6] = conjx(cmul(u[1], u[5]) - cmul(u[2], u[4]));
+  u[7] = conjx(cmul(u[2], u[3]) - cmul(u[0], u[5]));
+  u[8] = conjx(cmul(u[0], u[4]) - cmul(u[1], u[3]));
+}
+
+template <int P, bool C12>
+struct Link;
+
+template <bool C12>
+struct Link<P64, C12> {
+  using R = double;
+  static constexpr int kBytes = C12 ? 96 : 144;  // per site per direction
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<double> (&u)[9]) {
+    const double2* b = reinterpret_cast<const double2*>(base);
+    constexpr int n = C12 ? 6 : 9;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      double2 t = __ldg(b + (size_t)k * vh + s);
+      u[k] = cx(t.x, t.y);
+    }
+    if (C12) rebuild_row2(u);
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<double> (&u)[9]) {
+    double2* b = reinterpret_cast<double2*>(base);
+    constexpr int n = C12 ? 6 : 9;
+#pragma unroll
+    for (int k = 0; k < n; ++k) b[(size_t)k * vh + s] = make_double2(u[k].re, u[k].im);
+  }
+};
+
+template <>
+struct Link<P32, false> {
+  using R = float;
+  static constexpr int kBytes = 72;
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&u)[9]) {
+    const float2* b = reinterpret_cast<const float2*>(base);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      float2 t = __ldg(b + (size_t)k * vh + s);
+      u[k] = cx(t.x, t.y);
+    }
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&u)[9]) {
+    float2* b = reinterpret_cast<float2*>(base);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) b[(size_t)k * vh + s] = make_float2(u[k].re, u[k].im);
+  }
+};
+
+template <>
+struct Link<P32, true> {
+  using R = float;
+  static constexpr int kBytes = 48;
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&u)[9]) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float4 t = __ldg(b + (size_t)k * vh + s);
+      u[2 * k] = cx(t.x, t.y);
+      u[2 * k + 1] = cx(t.z, t.w);
+    }
+    rebuild_row2(u);
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&u)[9]) {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      b[(size_t)k * vh + s] = make_float4(u[2 * k].re, u[2 * k].im, u[2 * k + 1].re, u[2 * k + 1].im);
+  }
+};
+
+template <int P, bool C12>
+struct Link16 {
+  using R = float;
+  static constexpr int kBytes = C12 ? 24 : 36;
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&u)[9]) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(base) + s);
+    float2 f0 = H16<P>::to2(a.x), f1 = H16<P>::to2(a.y), f2 = H16<P>::to2(a.z), f3 = H16<P>::to2(a.w);
+    u[0] = cx(f0.x, f0.y);
+    u[1] = cx(f1.x, f1.y);
+    u[2] = cx(f2.x, f2.y);
+    u[3] = cx(f3.x, f3.y);
+    if (C12) {
+      const uint2 c = __ldg(reinterpret_cast<const uint2*>(base + (size_t)16 * vh) + s);
+      float2 g0 = H16<P>::to2(c.x), g1 = H16<P>::to2(c.y);
+      u[4] = cx(g0.x, g0.y);
+      u[5] = cx(g1.x, g1.y);
+      rebuild_row2(u);
+    } else {
+      const uint4 c = __ldg(reinterpret_cast<const uint4*>(base + (size_t)16 * vh) + s);
+      const uint32_t d = __ldg(reinterpret_cast<const uint32_t*>(base + (size_t)32 * vh) + s);
+      float2 g0 = H16<P>::to2(c.x), g1 = H16<P>::to2(c.y), g2 = H16<P>::to2(c.z), g3 = H16<P>::to2(c.w);
+      float2 g4 = H16<P>::to2(d);
+      u[4] = cx(g0.x, g0.y);
+      u[5] = cx(g1.x, g1.y);
+      u[6] = cx(g2.x, g2.y);
+      u[7] = cx(g3.x, g3.y);
+      u[8] = cx(g4.x, g4.y);
+    }
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&u)[9]) {
+    uint4 a;
+    a.x = H16<P>::from2(u[0].re, u[0].im);
+    a.y = H16<P>::from2(u[1].re, u[1].im);
+    a.z = H16<P>::from2(u[2].re, u[2].im);
+    a.w = H16<P>::from2(u[3].re, u[3].im);
+    reinterpret_cast<uint4*>(base)[s] = a;
+    if (C12) {
+      uint2 c;
+      c.x = H16<P>::from2(u[4].re, u[4].im);
+      c.y = H16<P>::from2(u[5].re, u[5].im);
+      reinterpret_cast<uint2*>(base + (size_t)16 * vh)[s] = c;
+    } else {
+      uint4 c;
+      c.x = H16<P>::from2(u[4].re, u[4].im);
+      c.y = H16<P>::from2(u[5].re, u[5].im);
+      c.z = H16<P>::from2(u[6].re, u[6].im);
+      c.w = H16<P>::from2(u[7].re, u[7].im);
+      reinterpret_cast<uint4*>(base + (size_t)16 * vh)[s] = c;
+      reinterpret_cast<uint32_t*>(base + (size_t)32 * vh)[s] = H16<P>::from2(u[8].re, u[8].im);
+    }
+  }
+};
+template <bool C12>
+struct Link<P16, C12> : Link16<P16, C12> {};
+template <bool C12>
+struct Link<PB16, C12> : Link16<PB16, C12> {};
+
+// ------------------------------------------------------------------ descriptors
+// A field reference inside a system: address of (rhs r, parity par) block is
+// p + r*rhs_stride + par*par_stride (bytes).  Parity-only fields use
+// par_stride = 0 and are only addressed with the parity they hold.
+struct Slot {
+  char* p;
+  long long rhs_stride;
+  long long par_stride;
+};
+
+enum SlotId {
+  S_LLO = 0,   // inner-precision links
+  S_LHI,       // FP64 links
+  S_B,         // user source (FP64, full)
+  S_X,         // user solution (FP64, full) -- the FP64 accumulator
+  S_BH,        // prepared even source (FP64)
+  S_RT,        // FP64 residual / temporary (full: even = r64, odd = t64)
+  S_XL,        // low-precision solution increment (accumulate precision)
+  S_R,         // inner residual
+  S_P,         // search direction
+  S_Z,         // D^dag r
+  S_W,         // D p
+  S_T,         // odd temporary (inner)
+  S_AUX0,      // operator/API use
+  S_AUX1,
+  S_AUX2,
+  S_AUX3,
+  kNumSlots
+};
+
+struct SysDesc {
+  int lxh, ly, lz, lt;  // Lx/2, Ly, Lz, Lt
+  int vh;               // sites per parity
+  int nrhs;
+  int anti_t;
+  int tpp;              // thread blocks per parity for this system
+  int tile0;            // first block (within one parity) of this system
+  int col0;             // first column (system, rhs) index
+  int part0;            // first partial-sum slot
+  int sys;              // system index
+  double kappa;
+  Slot f[kNumSlots];
+};
+
+// All systems of one launch, passed as a __grid_constant__ kernel parameter
+// (no descriptor buffers in device memory; CUDA graphs capture it by value).
+// Blocks [sd[i].tile0, sd[i].tile0 + sd[i].tpp) of each parity belong to
+// system i.
+constexpr int kMaxSys = 8;
+struct Batch {
+  int nsys;  // systems in this launch
+  int ntot;  // blocks per parity over all systems (grid x per parity)
+  int T;     // sites per block (per right-hand side), multiple of 32
+  int RB;    // right-hand sides per block (grid y = ceil(nrhs / RB))
+  SysDesc sd[kMaxSys];
+};
+
+__device__ __forceinline__ int block_system(const Batch& B, int b) {
+  int si = 0;
+  while (si + 1 < B.nsys && b >= B.sd[si + 1].tile0) ++si;
+  return si;
+}
+
+// Per-column (system, right-hand side) CG state, in device memory.
+struct ColState {
+  double gamma;    // |z|^2, z = A-side residual
+  double alpha, beta;
+  double rr;       // iterated |r|^2
+  double rr_ref;   // |r|^2 at the last reliable update
+  double bnorm2;   // |b|^2 (full lattice)
+  double tol2;     // tol^2 * |b|^2
+  double delta2;   // delta^2
+  double store[4]; // scalar outputs of plain reductions
+  unsigned long long deadline_ns;  // globaltimer deadline (0 = none)
+  int iter, maxiter, nrel;
+  int active;      // 1 while iterating
+  int do_rel;      // reliable update pending
+  int status;      // dw_status of this column
+  int pad[2];
+};
+
+// Batch-wide flags.
+struct Flags {
+  int active;      // number of active columns
+  int err;         // first device error code (0 = none)
+};
+
+enum Fin {
+  FIN_STORE0 = 0,  // store[0] = v  (plain reductions)
+  FIN_STORE1,
+  FIN_STORE2,
+  FIN_STORE3,
+  FIN_BNORM,       // bnorm2 = v, tol2 = tol^2 v (tol^2 kept in tol2 before)
+  FIN_ALPHA,       // alpha = gamma / v
+  FIN_UPDATE,      // rr = v; iter++; decide on a reliable update
+  FIN_RELIABLE,    // rr = rr_ref = v (true residual); convergence decision
+  FIN_GAMMA0,      // gamma = v, beta = 0
+  FIN_BETA,        // beta = v / gamma; gamma = v
+};
+
+struct RedArgs {
+  double* partial;
+  int* counter;
+  ColState* cols;
+  Flags* flags;
+  int fin;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void deactivate(ColState& C, Flags* F, int status) {
+  if (C.active) {
+    C.active = 0;
+    C.status = status;
+    atomicSub(&F->active, 1);
+  }
+}
+
+// CG scalar recurrences, run by one thread of the last block of a system.
+__device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
+  ColState& C = ra.cols[col];
+  switch (ra.fin) {
+    case FIN_STORE0: C.store[0] = v; break;
+    case FIN_STORE1: C.store[1] = v; break;
+    case FIN_STORE2: C.store[2] = v; break;
+    case FIN_STORE3: C.store[3] = v; break;
+    case FIN_BNORM: C.bnorm2 = v; C.tol2 = C.tol2 * v; break;
+    case FIN_ALPHA:
+      if (!C.active) break;
+      if (!(v > 0.0) || !isfinite(v) || !isfinite(C.gamma)) {
+        // p^dag A p <= 0 or not finite: CG cannot continue
+        deactivate(C, ra.flags, 7 /* DW_ERR_BREAKDOWN */);
+      } else {
+        C.alpha = C.gamma / v;
+      }
+      break;
+    case FIN_UPDATE: {
+      if (!C.active) break;
+      C.rr = v;
+      C.iter += 1;
+      bool timeout = C.deadline_ns != 0ull && globaltimer_ns() > C.deadline_ns;
+      if (!isfinite(v)) {
+        deactivate(C, ra.flags, 7);
+      } else if (v <= C.tol2 || v < C.delta2 * C.rr_ref || C.iter >= C.maxiter || timeout) {
+        C.do_rel = 1;
+      }
+      break;
+    }
+    case FIN_RELIABLE: {
+      if (!C.do_rel) break;
+      C.do_rel = 0;
+      C.rr = v;
+      C.rr_ref = v;
+      C.nrel += 1;
+      bool timeout = C.deadline_ns != 0ull && globaltimer_ns() > C.deadline_ns;
+      if (v <= C.tol2) deactivate(C, ra.flags, 0);
+      else if (!isfinite(v)) deactivate(C, ra.flags, 7);
+      else if (C.iter >= C.maxiter) deactivate(C, ra.flags, 6 /* NOT_CONVERGED */);
+      else if (timeout) deactivate(C, ra.flags, 8 /* TIMEOUT */);
+      break;
+    }
+    case FIN_GAMMA0:
+      if (!C.active) break;
+      C.gamma = v;
+      C.beta = 0.0;
+      break;
+    case FIN_BETA:
+      if (!C.active) break;
+      C.beta = v / C.gamma;
+      C.gamma = v;
+      break;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// A block holds RB groups of T threads (T a multiple of 32); group g works
+// on right-hand side r = blockIdx.y*RB + g.  Each group's values are summed in
+// a fixed order and written as this block's partial; the last block of the
+// system to arrive (per-system arrival counter, ntiles*gridDim.y arrivals)
+// sums every column's partials in a fixed order and runs the finalizer, so
+// results are bitwise reproducible run to run.  Every thread of the block
+// must call this.
+__device__ __forceinline__ void reduce_finalize(const SysDesc& S, int T, int RB, int tile, int ntiles, double v,
+                                                const RedArgs& ra) {
+  __shared__ double wsum[32];
+  __shared__ int am_last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  v = warp_sum(v);
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  const int wpr = T >> 5;
+  if (tid < RB) {
+    const int r = blockIdx.y * RB + tid;
+    if (r < S.nrhs) {
+      double s = 0.0;
+      for (int w = 0; w < wpr; ++w) s += wsum[tid * wpr + w];
+      ra.partial[S.part0 + r * ntiles + tile] = s;
+    }
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) am_last = (atomicAdd(&ra.counter[S.sys], 1) == ntiles * (int)gridDim.y - 1);
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  for (int r = 0; r < S.nrhs; ++r) {
+    double s = 0.0;
+    for (int i = tid; i < ntiles; i += blockDim.x) s += __ldcg(ra.partial + S.part0 + r * ntiles + i);
+    s = warp_sum(s);
+    __syncthreads();
+    if (lane == 0) wsum[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
+      finalize(ra, S.col0 + r, t);
+    }
+  }
+  if (tid == 0) ra.counter[S.sys] = 0;
+}
+
+// Cooperative copy of this block's system descriptor into shared memory.
+__device__ __forceinline__ void load_desc(SysDesc& S, const SysDesc* __restrict__ sd, int si) {
+  const int* src = reinterpret_cast<const int*>(sd + si);
+  int* dst = reinterpret_cast<int*>(&S);
+  for (int i = threadIdx.x; i < (int)(sizeof(SysDesc) / 4); i += blockDim.x) dst[i] = src[i];
+}
+
+}  // namespace dw

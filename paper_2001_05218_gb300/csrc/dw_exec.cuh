@@ -1,0 +1,103 @@
+// dw_exec.cuh -- launch helpers shared by the operator and solver translation units.
+#pragma once
+
+#include <cstdio>
+#include <string>
+
+#include "dw_internal.h"
+
+namespace dw {
+
+// Launch instrumentation (dw_profile_start / dw_profile_stop): counts every
+// kernel launch and brackets each stencil launch with CUDA events on its
+// stream, with the launch's algorithmic bytes and model flops.
+struct Profiler {
+  bool on = false;
+  long long launches = 0;
+  struct Rec {
+    int cat;
+    cudaEvent_t a, b;
+    double bytes, flops;
+  };
+  std::vector<std::string> names;
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  int category(const std::string& n) {
+    for (size_t i = 0; i < names.size(); ++i)
+      if (names[i] == n) return (int)i;
+    names.push_back(n);
+    return (int)names.size() - 1;
+  }
+  cudaEvent_t event() {
+    if (next == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[next++];
+  }
+};
+Profiler& profiler();
+inline void count_launch() {
+  Profiler& p = profiler();
+  if (p.on) p.launches += 1;
+}
+inline const char* prec_name(int p) { return p == P64 ? "f64" : p == P32 ? "f32" : p == P16 ? "f16" : "bf16"; }
+
+struct Exec {
+  Plan P;
+  RedBuf rb;
+  cudaStream_t st = nullptr;
+  RedArgs ra(int fin) const {
+    RedArgs a;
+    a.partial = rb.partial;
+    a.counter = rb.counter;
+    a.cols = rb.cols;
+    a.flags = rb.flags;
+    a.fin = fin;
+    return a;
+  }
+  dim3 grid(int par_mode) const { return par_mode == 2 ? P.grid2 : P.grid1; }
+};
+
+template <int SPA, int LP, bool C12, bool DAG, class In, class Epi>
+inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int fin = FIN_STORE0) {
+  Profiler& pr = profiler();
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (pr.on) {
+    pr.launches += 1;
+    ea = pr.event();
+    eb = pr.event();
+    cudaEventRecord(ea, E.st);
+  }
+  k_hop<SPA, LP, C12, DAG, In, Epi><<<E.grid(par_mode), E.P.block, 0, E.st>>>(E.P.B, par_mode, link_slot, in, epi,
+                                                                              E.ra(fin));
+  if (pr.on) {
+    cudaEventRecord(eb, E.st);
+    const int npar = par_mode == 2 ? 2 : 1;
+    double bytes = 0, sites = 0;
+    for (int i = 0; i < E.P.nsys; ++i) {
+      const double v = (double)E.P.B.sd[i].vh * npar;
+      bytes += v * 8.0 * Link<LP, C12>::kBytes + v * E.P.nrhs * (in.io_bytes() + epi.io_bytes());
+      sites += v * E.P.nrhs;
+    }
+    char nm[64];
+    snprintf(nm, sizeof nm, "hop %s/%s%s", prec_name(SPA), prec_name(LP), C12 ? "-c12" : "");
+    Profiler::Rec r;
+    r.cat = pr.category(nm);
+    r.a = ea;
+    r.b = eb;
+    r.bytes = bytes;
+    r.flops = 1320.0 * sites;
+    pr.recs.push_back(r);
+  }
+}
+
+template <int SP>
+inline void norm(const Exec& E, int par_mode, int slot, int fin) {
+  count_launch();
+  k_norm<SP><<<E.grid(par_mode), E.P.block, 0, E.st>>>(E.P.B, par_mode, slot, E.ra(fin));
+}
+
+}  // namespace dw

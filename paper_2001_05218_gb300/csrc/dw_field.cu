@@ -1,0 +1,526 @@
+// dw_field.cu -- field handles, host/device transfers and the layout kernels
+// that convert between the canonical (lexicographic, site-major complex128)
+// order and the even-odd structure-of-arrays storage.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "dw_exec.cuh"
+
+namespace dw {
+
+static thread_local char g_err[1024] = "";
+
+dw_status set_error(dw_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof g_err, fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+dw_status cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_err, sizeof g_err, "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file,
+           line);
+  return e == cudaErrorMemoryAllocation ? DW_ERR_OOM : DW_ERR_CUDA;
+}
+
+void clear_error() { g_err[0] = 0; }
+
+int spin_bytes(int prec) {
+  switch (prec) {
+    case DW_F64: return Spin<P64>::kBytes;
+    case DW_F32: return Spin<P32>::kBytes;
+    case DW_F16: return Spin<P16>::kBytes;
+    case DW_BF16: return Spin<PB16>::kBytes;
+  }
+  return 0;
+}
+
+int link_bytes(int prec, int c12) {
+  switch (prec) {
+    case DW_F64: return c12 ? Link<P64, true>::kBytes : Link<P64, false>::kBytes;
+    case DW_F32: return c12 ? Link<P32, true>::kBytes : Link<P32, false>::kBytes;
+    case DW_F16: return c12 ? Link<P16, true>::kBytes : Link<P16, false>::kBytes;
+    case DW_BF16: return c12 ? Link<PB16, true>::kBytes : Link<PB16, false>::kBytes;
+  }
+  return 0;
+}
+
+dw_status check_lattice(const dw_lattice* l) {
+  DW_CHECK(l != nullptr, DW_ERR_ARG, "lattice is NULL");
+  for (int m = 0; m < 4; ++m)
+    DW_CHECK(l->dims[m] >= 2 && (l->dims[m] % 2) == 0, DW_ERR_SHAPE,
+             "lattice extent %d in direction %d must be even and >= 2", l->dims[m], m);
+  const long long V = volume_of(*l);
+  DW_CHECK(V / 2 <= (1ll << 30), DW_ERR_SHAPE, "lattice too large (%lld sites)", V);
+  DW_CHECK((V / 2) % 8 == 0, DW_ERR_SHAPE, "half volume %lld must be a multiple of 8", V / 2);
+  return DW_OK;
+}
+
+bool same_dims(const dw_lattice& a, const dw_lattice& b) {
+  return a.dims[0] == b.dims[0] && a.dims[1] == b.dims[1] && a.dims[2] == b.dims[2] && a.dims[3] == b.dims[3];
+}
+
+Slot arena_slot(char* p, const dw_lattice& l, int prec, int nrhs, int npar) {
+  (void)nrhs;
+  Slot s;
+  const long long blk = (long long)spin_bytes(prec) * vh_of(l);
+  s.p = p;
+  s.par_stride = npar == 2 ? blk : 0;
+  s.rhs_stride = blk * npar;
+  return s;
+}
+
+Slot spinor_slot(const dw_field* f) { return arena_slot(f->ptr, f->lat, f->prec, f->nrhs, npar_of(f->kind)); }
+
+Slot gauge_slot(const char* p, const dw_lattice& l, int prec, int c12) {
+  Slot s;
+  s.p = const_cast<char*>(p);
+  s.rhs_stride = 0;
+  s.par_stride = 4ll * link_bytes(prec, c12) * vh_of(l);
+  return s;
+}
+
+void geometry(SysDesc& S, const dw_lattice& l, int nrhs) {
+  memset(&S, 0, sizeof S);
+  S.lxh = l.dims[0] / 2;
+  S.ly = l.dims[1];
+  S.lz = l.dims[2];
+  S.lt = l.dims[3];
+  S.vh = (int)vh_of(l);
+  S.nrhs = nrhs;
+  S.anti_t = l.t_antiperiodic ? 1 : 0;
+  S.kappa = l.kappa;
+}
+
+void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T) {
+  memset(&P.B, 0, sizeof P.B);
+  P.nsys = (int)lats.size();
+  P.nrhs = nrhs;
+  int RB = 1;
+  if (nrhs > 1) {
+    T = 64;
+    for (int d = 4; d >= 1; --d)
+      if (nrhs % d == 0) { RB = d; break; }
+  } else if (T <= 0) {
+    T = 128;
+  }
+  P.B.nsys = P.nsys;
+  P.B.T = T;
+  P.B.RB = RB;
+  int tile = 0, part = 0;
+  for (int i = 0; i < P.nsys; ++i) {
+    SysDesc& S = P.B.sd[i];
+    geometry(S, lats[i], nrhs);
+    S.tpp = (S.vh + T - 1) / T;
+    S.tile0 = tile;
+    S.col0 = i * nrhs;
+    S.part0 = part;
+    S.sys = i;
+    tile += S.tpp;
+    part += nrhs * 2 * S.tpp;
+  }
+  P.B.ntot = tile;
+  P.ncols = P.nsys * nrhs;
+  P.partials = part;
+  const int gy = (nrhs + RB - 1) / RB;
+  P.block = dim3(T * RB);
+  P.grid1 = dim3(tile, gy);
+  P.grid2 = dim3(2 * tile, gy);
+}
+
+// ------------------------------------------------------------------ layout kernels
+__host__ __device__ inline long long lex_of(const int* d, int par, long long j) {
+  const int lxh = d[0] / 2;
+  long long q = j / lxh;
+  const int xh = (int)(j - q * lxh);
+  const int y = (int)(q % d[1]);
+  q /= d[1];
+  const int z = (int)(q % d[2]);
+  const int t = (int)(q / d[2]);
+  const int x = 2 * xh + ((y + z + t + par) & 1);
+  return x + (long long)d[0] * (y + (long long)d[1] * (z + (long long)d[2] * t));
+}
+
+struct Dims4 {
+  int d[4];
+};
+
+// canonical (complex128, [rhs][site][12]) -> storage; full: site = lex, parity
+// field: site = j.  One thread per (parity, j), loop over rhs.
+template <int P>
+__global__ void k_pack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, const double2* __restrict__ can,
+                              Slot dst) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int pi = blockIdx.y;  // parity index within the field
+  if (j >= vh) return;
+  const int par = npar == 2 ? pi : par0;
+  const long long site = npar == 2 ? lex_of(dm.d, par, j) : j;
+  const long long nsite = (long long)vh * npar;
+  using R = typename Spin<P>::R;
+  for (int r = 0; r < nrhs; ++r) {
+    const double2* src = can + ((long long)r * nsite + site) * 12;
+    Cx<R> v[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double2 t = src[k];
+      v[k] = cx((R)t.x, (R)t.y);
+    }
+    Spin<P>::store(dst.p + r * dst.rhs_stride + pi * dst.par_stride, vh, (int)j, v);
+  }
+}
+
+template <int P>
+__global__ void k_unpack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, Slot srcs, double2* __restrict__ can) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int pi = blockIdx.y;
+  if (j >= vh) return;
+  const int par = npar == 2 ? pi : par0;
+  const long long site = npar == 2 ? lex_of(dm.d, par, j) : j;
+  const long long nsite = (long long)vh * npar;
+  using R = typename Spin<P>::R;
+  for (int r = 0; r < nrhs; ++r) {
+    Cx<R> v[12];
+    Spin<P>::load(srcs.p + r * srcs.rhs_stride + pi * srcs.par_stride, vh, (int)j, v);
+    double2* o = can + ((long long)r * nsite + site) * 12;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = make_double2((double)v[k].re, (double)v[k].im);
+  }
+}
+
+template <int P, bool C12>
+__global__ void k_pack_gauge(Dims4 dm, int vh, const double2* __restrict__ can, char* dst) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int par = blockIdx.y;
+  if (j >= vh) return;
+  const long long site = lex_of(dm.d, par, j);
+  const long long lb = (long long)Link<P, C12>::kBytes * vh;
+  using R = typename Link<P, C12>::R;
+  for (int mu = 0; mu < 4; ++mu) {
+    const double2* src = can + (site * 4 + mu) * 9;
+    Cx<R> u[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      double2 t = src[k];
+      u[k] = cx((R)t.x, (R)t.y);
+    }
+    Link<P, C12>::store(dst + par * 4 * lb + mu * lb, vh, (int)j, u);
+  }
+}
+
+template <int P, bool C12>
+__global__ void k_unpack_gauge(Dims4 dm, int vh, const char* src, double2* __restrict__ can) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int par = blockIdx.y;
+  if (j >= vh) return;
+  const long long site = lex_of(dm.d, par, j);
+  const long long lb = (long long)Link<P, C12>::kBytes * vh;
+  using R = typename Link<P, C12>::R;
+  for (int mu = 0; mu < 4; ++mu) {
+    Cx<R> u[9];
+    Link<P, C12>::load(src + par * 4 * lb + mu * lb, vh, (int)j, u);
+    double2* o = can + (site * 4 + mu) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) o[k] = make_double2((double)u[k].re, (double)u[k].im);
+  }
+}
+
+// FP64 18-real links -> (P, C12) storage
+template <int P, bool C12>
+__global__ void k_convert_gauge(int vh, const char* src, char* dst) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int pm = blockIdx.y;  // parity*4 + mu
+  if (j >= vh) return;
+  const long long lsrc = (long long)Link<P64, false>::kBytes * vh;
+  const long long ldst = (long long)Link<P, C12>::kBytes * vh;
+  Cx<double> u[9];
+  Link<P64, false>::load(src + pm * lsrc, vh, (int)j, u);
+  using R = typename Link<P, C12>::R;
+  Cx<R> v[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) v[k] = cx((R)u[k].re, (R)u[k].im);
+  Link<P, C12>::store(dst + pm * ldst, vh, (int)j, v);
+}
+
+static Dims4 dims4(const dw_lattice& l) {
+  Dims4 d;
+  for (int m = 0; m < 4; ++m) d.d[m] = l.dims[m];
+  return d;
+}
+
+#define DW_PREC_DISPATCH(prec, BODY)         \
+  switch (prec) {                            \
+    case DW_F64: { constexpr int PP = P64; BODY; } break;  \
+    case DW_F32: { constexpr int PP = P32; BODY; } break;  \
+    case DW_F16: { constexpr int PP = P16; BODY; } break;  \
+    case DW_BF16: { constexpr int PP = PB16; BODY; } break; \
+  }
+
+dw_status pack_spinor_from_canonical(dw_field* f, const double* dev, cudaStream_t st) {
+  const int vh = (int)vh_of(f->lat);
+  const int npar = npar_of(f->kind);
+  const int par0 = f->kind == DW_SPINOR_ODD ? 1 : 0;
+  dim3 b(256), g((vh + 255) / 256, npar);
+  Slot s = spinor_slot(f);
+  const double2* c = reinterpret_cast<const double2*>(dev);
+  DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_spinor<PP><<<g, b, 0, st>>>(dims4(f->lat), vh, f->nrhs, npar, par0, c, s)));
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+
+dw_status unpack_spinor_to_canonical(const dw_field* f, double* dev, cudaStream_t st) {
+  const int vh = (int)vh_of(f->lat);
+  const int npar = npar_of(f->kind);
+  const int par0 = f->kind == DW_SPINOR_ODD ? 1 : 0;
+  dim3 b(256), g((vh + 255) / 256, npar);
+  Slot s = spinor_slot(f);
+  double2* c = reinterpret_cast<double2*>(dev);
+  DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_spinor<PP><<<g, b, 0, st>>>(dims4(f->lat), vh, f->nrhs, npar, par0, s, c)));
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+
+static dw_status pack_gauge(dw_field* f, const double* dev, cudaStream_t st) {
+  const int vh = (int)vh_of(f->lat);
+  dim3 b(256), g((vh + 255) / 256, 2);
+  const double2* c = reinterpret_cast<const double2*>(dev);
+  if (f->compress12) {
+    DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_gauge<PP, true><<<g, b, 0, st>>>(dims4(f->lat), vh, c, f->ptr)));
+  } else {
+    DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_gauge<PP, false><<<g, b, 0, st>>>(dims4(f->lat), vh, c, f->ptr)));
+  }
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+
+static dw_status unpack_gauge(const dw_field* f, double* dev, cudaStream_t st) {
+  const int vh = (int)vh_of(f->lat);
+  dim3 b(256), g((vh + 255) / 256, 2);
+  double2* c = reinterpret_cast<double2*>(dev);
+  if (f->compress12) {
+    DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_gauge<PP, true><<<g, b, 0, st>>>(dims4(f->lat), vh, f->ptr, c)));
+  } else {
+    DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_gauge<PP, false><<<g, b, 0, st>>>(dims4(f->lat), vh, f->ptr, c)));
+  }
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+
+dw_status derived_links(dw_field* U, int prec, int c12, cudaStream_t st, const char** out) {
+  if (prec == (int)U->prec && c12 == U->compress12) {
+    *out = U->ptr;
+    return DW_OK;
+  }
+  DW_CHECK(U->prec == DW_F64 && !U->compress12, DW_ERR_PRECISION,
+           "derived link copies need an FP64 18-real gauge field");
+  for (auto& d : U->derived)
+    if (d.prec == prec && d.c12 == c12) {
+      if (d.version != U->version) {
+        const int vh = (int)vh_of(U->lat);
+        dim3 b(256), g((vh + 255) / 256, 8);
+        if (c12) {
+          DW_PREC_DISPATCH(prec, (count_launch(), k_convert_gauge<PP, true><<<g, b, 0, st>>>(vh, U->ptr, d.ptr)));
+        } else {
+          DW_PREC_DISPATCH(prec, (count_launch(), k_convert_gauge<PP, false><<<g, b, 0, st>>>(vh, U->ptr, d.ptr)));
+        }
+        DW_CUDA(cudaGetLastError());
+        d.version = U->version;
+      }
+      *out = d.ptr;
+      return DW_OK;
+    }
+  dw_field::Derived d;
+  d.prec = prec;
+  d.c12 = c12;
+  d.bytes = 8ull * link_bytes(prec, c12) * vh_of(U->lat);
+  DW_CUDA(cudaMalloc(&d.ptr, d.bytes));
+  d.version = U->version - 1;  // force conversion below
+  U->derived.push_back(d);
+  return derived_links(U, prec, c12, st, out);
+}
+
+}  // namespace dw
+
+namespace dw {
+Profiler& profiler() {
+  static Profiler p;
+  return p;
+}
+}  // namespace dw
+
+using namespace dw;
+
+extern "C" {
+
+const char* dw_last_error(void) { return g_err; }
+
+dw_status dw_profile_start(void) {
+  Profiler& p = profiler();
+  p.on = true;
+  p.launches = 0;
+  p.recs.clear();
+  p.next = 0;
+  return DW_OK;
+}
+
+dw_status dw_profile_stop(dw_profile_entry* out, int max_entries, int* n_entries, long long* launches) {
+  Profiler& p = profiler();
+  DW_CUDA(cudaDeviceSynchronize());
+  std::vector<dw_profile_entry> agg(p.names.size());
+  for (size_t i = 0; i < agg.size(); ++i) {
+    memset(&agg[i], 0, sizeof agg[i]);
+    snprintf(agg[i].name, sizeof agg[i].name, "%s", p.names[i].c_str());
+  }
+  for (auto& r : p.recs) {
+    float ms = 0.f;
+    DW_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+    dw_profile_entry& e = agg[r.cat];
+    e.launches += 1;
+    e.total_ms += ms;
+    e.bytes += r.bytes;
+    e.flops += r.flops;
+  }
+  int n = 0;
+  for (auto& e : agg)
+    if (e.launches > 0) {
+      if (out && n < max_entries) out[n] = e;
+      ++n;
+    }
+  if (n_entries) *n_entries = n;
+  if (launches) *launches = p.launches;
+  p.on = false;
+  p.recs.clear();
+  p.next = 0;
+  return DW_OK;
+}
+
+const char* dw_version(void) { return "dw 1.0 (sm_103a)"; }
+
+dw_status dw_field_bytes(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs,
+                         size_t* bytes) {
+  DW_TRY(check_lattice(lat));
+  DW_CHECK(bytes != nullptr, DW_ERR_ARG, "bytes is NULL");
+  DW_CHECK(prec >= DW_F64 && prec <= DW_BF16, DW_ERR_PRECISION, "unknown precision %d", (int)prec);
+  DW_CHECK(kind >= DW_GAUGE && kind <= DW_SPINOR_ODD, DW_ERR_ARG, "unknown field kind %d", (int)kind);
+  const long long vh = vh_of(*lat);
+  if (kind == DW_GAUGE) {
+    DW_CHECK(nrhs == 1 || nrhs == 0, DW_ERR_SHAPE, "gauge fields have nrhs = 1");
+    *bytes = 8ull * link_bytes(prec, compress12 ? 1 : 0) * vh;
+  } else {
+    DW_CHECK(nrhs >= 1 && nrhs <= 64, DW_ERR_SHAPE, "nrhs %d out of range 1..64", nrhs);
+    DW_CHECK(!compress12, DW_ERR_ARG, "compress12 applies to gauge fields only");
+    *bytes = (size_t)nrhs * npar_of(kind) * spin_bytes(prec) * vh;
+  }
+  return DW_OK;
+}
+
+static dw_status make_field(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs, void* ptr,
+                            size_t have, int owned, dw_field** out) {
+  size_t need = 0;
+  DW_TRY(dw_field_bytes(lat, kind, prec, compress12, nrhs, &need));
+  DW_CHECK(out != nullptr, DW_ERR_ARG, "out is NULL");
+  dw_field* f = new dw_field();
+  f->lat = *lat;
+  f->kind = kind;
+  f->prec = prec;
+  f->compress12 = compress12 ? 1 : 0;
+  f->nrhs = kind == DW_GAUGE ? 1 : nrhs;
+  f->bytes = need;
+  f->owned = owned;
+  f->version = 1;
+  cudaGetDevice(&f->device);
+  if (owned) {
+    cudaError_t e = cudaMalloc(&f->ptr, need);
+    if (e != cudaSuccess) {
+      delete f;
+      return cuda_error(e, "cudaMalloc(field)", __FILE__, __LINE__);
+    }
+  } else {
+    if (ptr == nullptr || have < need || (reinterpret_cast<uintptr_t>(ptr) & 255) != 0) {
+      delete f;
+      return set_error(DW_ERR_ARG, "wrapped memory must be non-NULL, 256-byte aligned and >= %zu bytes", need);
+    }
+    f->ptr = static_cast<char*>(ptr);
+  }
+  *out = f;
+  return DW_OK;
+}
+
+dw_status dw_field_alloc(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs,
+                         dw_field** out) {
+  return make_field(lat, kind, prec, compress12, nrhs, nullptr, 0, 1, out);
+}
+
+dw_status dw_field_wrap(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs, void* dev_ptr,
+                        size_t bytes, dw_field** out) {
+  return make_field(lat, kind, prec, compress12, nrhs, dev_ptr, bytes, 0, out);
+}
+
+dw_status dw_field_free(dw_field* f) {
+  if (f == nullptr) return DW_OK;
+  cudaDeviceSynchronize();
+  for (auto& d : f->derived) cudaFree(d.ptr);
+  if (f->owned) cudaFree(f->ptr);
+  delete f;
+  return DW_OK;
+}
+
+dw_status dw_field_info(const dw_field* f, dw_lattice* lat, dw_kind* kind, dw_prec* prec, int* compress12,
+                        int* nrhs) {
+  DW_CHECK(f != nullptr, DW_ERR_ARG, "field is NULL");
+  if (lat) *lat = f->lat;
+  if (kind) *kind = f->kind;
+  if (prec) *prec = f->prec;
+  if (compress12) *compress12 = f->compress12;
+  if (nrhs) *nrhs = f->nrhs;
+  return DW_OK;
+}
+
+static size_t canonical_bytes(const dw_field* f) {
+  const long long V = volume_of(f->lat);
+  if (f->kind == DW_GAUGE) return (size_t)V * 4 * 9 * 16;
+  return (size_t)f->nrhs * (f->kind == DW_SPINOR_FULL ? V : V / 2) * 12 * 16;
+}
+
+dw_status dw_field_import(dw_field* f, const double* dev, dw_stream_t stream) {
+  DW_CHECK(f != nullptr && dev != nullptr, DW_ERR_ARG, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  f->version += 1;
+  if (f->kind == DW_GAUGE) return pack_gauge(f, dev, st);
+  return pack_spinor_from_canonical(f, dev, st);
+}
+
+dw_status dw_field_export(const dw_field* f, double* dev, dw_stream_t stream) {
+  DW_CHECK(f != nullptr && dev != nullptr, DW_ERR_ARG, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (f->kind == DW_GAUGE) return unpack_gauge(f, dev, st);
+  return unpack_spinor_to_canonical(f, dev, st);
+}
+
+dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream) {
+  DW_CHECK(f != nullptr && host != nullptr, DW_ERR_ARG, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t nb = canonical_bytes(f);
+  void* tmp = nullptr;
+  DW_CUDA(cudaMallocAsync(&tmp, nb, st));
+  DW_CUDA(cudaMemcpyAsync(tmp, host, nb, cudaMemcpyHostToDevice, st));
+  dw_status s = dw_field_import(f, static_cast<const double*>(tmp), stream);
+  cudaFreeAsync(tmp, st);
+  return s;
+}
+
+dw_status dw_field_download(const dw_field* f, double* host, dw_stream_t stream) {
+  DW_CHECK(f != nullptr && host != nullptr, DW_ERR_ARG, "NULL argument");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t nb = canonical_bytes(f);
+  void* tmp = nullptr;
+  DW_CUDA(cudaMallocAsync(&tmp, nb, st));
+  dw_status s = dw_field_export(f, static_cast<double*>(tmp), stream);
+  if (s == DW_OK) DW_CUDA(cudaMemcpyAsync(host, tmp, nb, cudaMemcpyDeviceToHost, st));
+  cudaFreeAsync(tmp, st);
+  return s;
+}
+
+}  // extern "C"

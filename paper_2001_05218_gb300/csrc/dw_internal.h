@@ -1,0 +1,97 @@
+// dw_internal.h -- host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+
+#include "dw.h"
+#include "dw_kernels.cuh"
+
+struct dw_field {
+  dw_lattice lat;
+  dw_kind kind;
+  dw_prec prec;
+  int compress12;
+  int nrhs;
+  char* ptr;
+  size_t bytes;
+  int owned;
+  int device;
+  unsigned long long version;  // bumped by every upload/import
+  // gauge fields: cached copies in other storage formats (solver inner links)
+  struct Derived {
+    int prec, c12;
+    char* ptr;
+    size_t bytes;
+    unsigned long long version;
+  };
+  std::vector<Derived> derived;
+};
+
+namespace dw {
+
+dw_status set_error(dw_status st, const char* fmt, ...);
+dw_status cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void clear_error();
+
+#define DW_CUDA(call)                                                   \
+  do {                                                                  \
+    cudaError_t e_ = (call);                                            \
+    if (e_ != cudaSuccess) return ::dw::cuda_error(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define DW_CHECK(cond, st, ...)                          \
+  do {                                                   \
+    if (!(cond)) return ::dw::set_error(st, __VA_ARGS__); \
+  } while (0)
+
+#define DW_TRY(expr)                   \
+  do {                                 \
+    dw_status s_ = (expr);             \
+    if (s_ != DW_OK) return s_;        \
+  } while (0)
+
+inline long long volume_of(const dw_lattice& l) {
+  return (long long)l.dims[0] * l.dims[1] * l.dims[2] * l.dims[3];
+}
+inline long long vh_of(const dw_lattice& l) { return volume_of(l) / 2; }
+
+int spin_bytes(int prec);             // bytes per site of one spinor
+int link_bytes(int prec, int c12);    // bytes per site per direction
+dw_status check_lattice(const dw_lattice* l);
+bool same_dims(const dw_lattice& a, const dw_lattice& b);
+inline int npar_of(dw_kind k) { return k == DW_SPINOR_FULL ? 2 : 1; }
+
+// Slot of a spinor field: rhs and parity strides in bytes.
+Slot spinor_slot(const dw_field* f);
+// Slot of a spinor arena laid out like a field of the given kind/prec.
+Slot arena_slot(char* p, const dw_lattice& l, int prec, int nrhs, int npar);
+// Slot of a gauge field stored at p (parity stride = 4 directions).
+Slot gauge_slot(const char* p, const dw_lattice& l, int prec, int c12);
+void geometry(SysDesc& S, const dw_lattice& l, int nrhs);
+
+// Launch plan for a set of systems sharing nrhs.
+struct Plan {
+  Batch B;
+  int nsys = 0, nrhs = 1, ncols = 0;
+  int partials = 0;  // doubles in the partial-sum buffer
+  dim3 block, grid1, grid2;  // one parity / both parities
+};
+void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T);
+
+// Device scratch for reductions of one plan.
+struct RedBuf {
+  double* partial = nullptr;
+  int* counter = nullptr;
+  ColState* cols = nullptr;
+  Flags* flags = nullptr;
+};
+
+// Gauge field copy in (prec, c12) storage, cached on the handle.
+dw_status derived_links(dw_field* U, int prec, int c12, cudaStream_t st, const char** out);
+
+dw_status pack_spinor_from_canonical(dw_field* f, const double* dev, cudaStream_t st);
+dw_status unpack_spinor_to_canonical(const dw_field* f, double* dev, cudaStream_t st);
+
+}  // namespace dw

@@ -1,0 +1,516 @@
+// dw_kernels.cuh -- the hopping-term stencil and the CG vector kernels.
+//
+// Hopping term (the sum in D = 1 - kappa*H):
+//   (H psi)(x) = sum_mu [ (1 - gamma_mu) eta U_mu(x) psi(x+mu)
+//                       + (1 + gamma_mu) eta U_mu(x-mu)^dag psi(x-mu) ]
+// and for D^dag the two projectors swap.  Per output site and direction the
+// kernel spin-projects the neighbour to a half spinor (2 spins x 3 colours),
+// multiplies by the link or its adjoint, and reconstructs the lower two spins
+// (the four stages of the paper's Fig. 1: load, linear combination, 3x3
+// mat-vec, accumulate).  One thread per (output site, right-hand side);
+// threads of a warp take consecutive even-odd site indices so every load is
+// a coalesced 16-byte (or 8-byte) access.  The boundary sign eta (-1 on links
+// crossing t = Lt-1 -> 0 when antiperiodic) is applied in the kernel, so
+// links stay SU(3) and 12-real compression stays valid.
+//
+// Gamma basis (chiral): gamma_mu = [[0, B_mu], [B_mu^dag, 0]] with
+// B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.  Then
+//   (1 + s gamma_mu) psi = [ h ; s B^dag h ],  h = psi_up + s B psi_down.
+#pragma once
+
+#include "dw_common.cuh"
+
+namespace dw {
+
+enum Coef { C_ONE = 0, C_MK, C_PK, C_MK2, C_PK2 };
+enum Gate { G_ACTIVE = 0, G_REL, G_ALL };
+
+template <int C>
+__device__ __forceinline__ double coef_of(double kappa) {
+  return C == C_ONE ? 1.0 : C == C_MK ? -kappa : C == C_PK ? kappa : C == C_MK2 ? -kappa * kappa : kappa * kappa;
+}
+
+__device__ __forceinline__ int gate_of(int g, const ColState* cols, int col) {
+  if (g == G_ALL) return 1;
+  return g == G_ACTIVE ? cols[col].active : cols[col].do_rel;
+}
+
+// a + S*b,  S = +1 or -1 (compile time)
+template <int S, typename R>
+__device__ __forceinline__ Cx<R> pm(Cx<R> a, Cx<R> b) { return S > 0 ? a + b : a - b; }
+
+// half spinor of (1 + S gamma_mu) psi
+template <int MU, int S, typename R>
+__device__ __forceinline__ void project(const Cx<R> (&p)[12], Cx<R> (&h)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) {        // h0 = p0 - S i p3, h1 = p1 - S i p2
+      h[c] = pm<-S>(p[c], mul_i(p[9 + c]));
+      h[3 + c] = pm<-S>(p[3 + c], mul_i(p[6 + c]));
+    } else if (MU == 1) { // h0 = p0 - S p3, h1 = p1 + S p2
+      h[c] = pm<-S>(p[c], p[9 + c]);
+      h[3 + c] = pm<S>(p[3 + c], p[6 + c]);
+    } else if (MU == 2) { // h0 = p0 - S i p2, h1 = p1 + S i p3
+      h[c] = pm<-S>(p[c], mul_i(p[6 + c]));
+      h[3 + c] = pm<S>(p[3 + c], mul_i(p[9 + c]));
+    } else {              // h0 = p0 + S p2, h1 = p1 + S p3
+      h[c] = pm<S>(p[c], p[6 + c]);
+      h[3 + c] = pm<S>(p[3 + c], p[9 + c]);
+    }
+  }
+}
+
+// acc += (1 + S gamma_mu) reconstructed from the multiplied half spinor g
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accumulate(Cx<R> (&acc)[12], const Cx<R> (&g)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = acc[c] + g[c];
+    acc[3 + c] = acc[3 + c] + g[3 + c];
+    if (MU == 0) {        // lower = S i (g1, g0)
+      acc[6 + c] = pm<S>(acc[6 + c], mul_i(g[3 + c]));
+      acc[9 + c] = pm<S>(acc[9 + c], mul_i(g[c]));
+    } else if (MU == 1) { // lower = S (g1, -g0)
+      acc[6 + c] = pm<S>(acc[6 + c], g[3 + c]);
+      acc[9 + c] = pm<-S>(acc[9 + c], g[c]);
+    } else if (MU == 2) { // lower = S i (g0, -g1)
+      acc[6 + c] = pm<S>(acc[6 + c], mul_i(g[c]));
+      acc[9 + c] = pm<-S>(acc[9 + c], mul_i(g[3 + c]));
+    } else {              // lower = S (g0, g1)
+      acc[6 + c] = pm<S>(acc[6 + c], g[c]);
+      acc[9 + c] = pm<S>(acc[9 + c], g[3 + c]);
+    }
+  }
+}
+
+// g = U h (ADJ = false) or U^dag h (ADJ = true), on both half-spinor spins
+template <bool ADJ, typename R>
+__device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6], Cx<R> (&g)[6]) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (!ADJ) {
+        Cx<R> t = cmul(u[a * 3 + 0], h[3 * k + 0]);
+        t = cmadd(u[a * 3 + 1], h[3 * k + 1], t);
+        g[3 * k + a] = cmadd(u[a * 3 + 2], h[3 * k + 2], t);
+      } else {
+        Cx<R> t = cjmul(u[0 * 3 + a], h[3 * k + 0]);
+        t = cjmadd(u[1 * 3 + a], h[3 * k + 1], t);
+        g[3 * k + a] = cjmadd(u[2 * 3 + a], h[3 * k + 2], t);
+      }
+    }
+}
+
+// Site coordinates of even-odd index s on parity par.
+struct Coord {
+  int xh, x, y, z, t, row;  // row = s - xh (start of the x-row in eo indexing)
+};
+
+__device__ __forceinline__ Coord coord_of(const SysDesc& S, int s, int par) {
+  Coord c;
+  int q = s / S.lxh;
+  c.xh = s - q * S.lxh;
+  c.row = s - c.xh;
+  c.y = q % S.ly;
+  q /= S.ly;
+  c.z = q % S.lz;
+  c.t = q / S.lz;
+  c.x = 2 * c.xh + ((c.y + c.z + c.t + par) & 1);
+  return c;
+}
+
+// eo index of the neighbour one step in direction MU (DIR = +1/-1); *eta is
+// the boundary sign of the link crossed.
+template <int MU, int DIR>
+__device__ __forceinline__ int neighbour(const SysDesc& S, const Coord& c, int s, float* eta) {
+  *eta = 1.f;
+  if (MU == 0) {
+    const int lx = 2 * S.lxh;
+    int xn = c.x + DIR;
+    xn = xn == lx ? 0 : (xn < 0 ? lx - 1 : xn);
+    return (xn >> 1) + c.row;
+  } else if (MU == 1) {
+    const int st = S.lxh;
+    if (DIR > 0) return c.y == S.ly - 1 ? s - (S.ly - 1) * st : s + st;
+    return c.y == 0 ? s + (S.ly - 1) * st : s - st;
+  } else if (MU == 2) {
+    const int st = S.lxh * S.ly;
+    if (DIR > 0) return c.z == S.lz - 1 ? s - (S.lz - 1) * st : s + st;
+    return c.z == 0 ? s + (S.lz - 1) * st : s - st;
+  } else {
+    const int st = S.lxh * S.ly * S.lz;
+    if (DIR > 0) {
+      if (c.t == S.lt - 1) {
+        if (S.anti_t) *eta = -1.f;
+        return s - (S.lt - 1) * st;
+      }
+      return s + st;
+    }
+    if (c.t == 0) {
+      if (S.anti_t) *eta = -1.f;
+      return s + (S.lt - 1) * st;
+    }
+    return s - st;
+  }
+}
+
+__device__ __forceinline__ const char* slot_ptr(const SysDesc& S, int slot, int r, int par) {
+  const Slot& f = S.f[slot];
+  return f.p + r * f.rhs_stride + par * f.par_stride;
+}
+__device__ __forceinline__ char* slot_wptr(const SysDesc& S, int slot, int r, int par) {
+  const Slot& f = S.f[slot];
+  return f.p + r * f.rhs_stride + par * f.par_stride;
+}
+
+template <typename R, typename Q>
+__device__ __forceinline__ void convert12(const Cx<Q> (&a)[12], Cx<R> (&b)[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) b[k] = cx((R)a[k].re, (R)a[k].im);
+}
+
+// ------------------------------------------------------------------ input loaders
+// Neighbour spinor from one field.
+template <int SP>
+struct InOne {
+  int slot;
+  static const char* name() { return "one"; }
+  __host__ double io_bytes() const { return Spin<SP>::kBytes; }
+  template <typename R>
+  __device__ __forceinline__ void load(const SysDesc& S, int par, int r, int s, Cx<R> (&v)[12]) const {
+    Cx<typename Spin<SP>::R> t[12];
+    Spin<SP>::load(slot_ptr(S, slot, r, par), S.vh, s, t);
+    convert12(t, v);
+  }
+};
+
+// Neighbour spinor x + xl: the FP64 accumulator plus the low-precision increment.
+template <int SPL>
+struct InSum {
+  int slot_x, slot_xl;
+  __host__ double io_bytes() const { return Spin<P64>::kBytes + Spin<SPL>::kBytes; }
+  template <typename R>
+  __device__ __forceinline__ void load(const SysDesc& S, int par, int r, int s, Cx<R> (&v)[12]) const {
+    Cx<double> a[12];
+    Cx<typename Spin<SPL>::R> b[12];
+    Spin<P64>::load(slot_ptr(S, slot_x, r, par), S.vh, s, a);
+    Spin<SPL>::load(slot_ptr(S, slot_xl, r, par), S.vh, s, b);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = cx((R)(a[k].re + (double)b[k].re), (R)(a[k].im + (double)b[k].im));
+  }
+};
+
+// ------------------------------------------------------------------ epilogues
+// out = coef * H in
+template <int SPO, int COEF>
+struct EpiOut {
+  static constexpr bool kReduce = false;
+  int slot_out;
+  int gate;
+  __host__ double io_bytes() const { return Spin<SPO>::kBytes; }
+  template <typename R>
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12], double&) const {
+    using RO = typename Spin<SPO>::R;
+    const R c = (R)coef_of<COEF>(S.kappa);
+    Cx<RO> o[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o[k] = cx((RO)(c * acc[k].re), (RO)(c * acc[k].im));
+    Spin<SPO>::store(slot_wptr(S, slot_out, r, par), S.vh, s, o);
+  }
+};
+
+// out = X + coef * H in  (X on the output parity), optional |out|^2 reduction.
+// slot_out < 0: nothing stored (norm only).
+template <int SPO, int SPX, int COEF, bool RED>
+struct EpiXpay {
+  static constexpr bool kReduce = RED;
+  int slot_out, slot_x;
+  int gate;
+  __host__ double io_bytes() const { return Spin<SPX>::kBytes + (slot_out >= 0 ? Spin<SPO>::kBytes : 0); }
+  template <typename R>
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12], double& nrm) const {
+    using RO = typename Spin<SPO>::R;
+    Cx<typename Spin<SPX>::R> xv[12];
+    Spin<SPX>::load(slot_ptr(S, slot_x, r, par), S.vh, s, xv);
+    const R c = (R)coef_of<COEF>(S.kappa);
+    Cx<RO> o[12];
+    R n = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      R re = fma(c, acc[k].re, (R)xv[k].re), im = fma(c, acc[k].im, (R)xv[k].im);
+      o[k] = cx((RO)re, (RO)im);
+      n = fma(re, re, fma(im, im, n));
+    }
+    nrm = (double)n;
+    if (slot_out >= 0) Spin<SPO>::store(slot_wptr(S, slot_out, r, par), S.vh, s, o);
+  }
+};
+
+// Reliable update on the even-odd system (FP64), at even site s:
+//   x <- x + xl;  xl <- 0;  r64 = bh - x + kappa^2 * acc  (acc = H_eo t64);
+//   r_low <- r64;  reduction |r64|^2.
+template <int SPL, int SPA>
+struct EpiReliableEO {
+  static constexpr bool kReduce = true;
+  int gate;
+  __host__ double io_bytes() const {
+    return 4.0 * Spin<P64>::kBytes + 2.0 * Spin<SPA>::kBytes + Spin<SPL>::kBytes;
+  }
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<double> (&acc)[12],
+                                        double& nrm) const {
+    Cx<double> x[12], bh[12], rv[12];
+    Cx<typename Spin<SPA>::R> xl[12];
+    Spin<P64>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
+    Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
+    Spin<P64>::load(slot_ptr(S, S_BH, r, par), S.vh, s, bh);
+    const double k2 = S.kappa * S.kappa;
+    double n = 0;
+    Cx<typename Spin<SPA>::R> zero[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      x[k] = cx(x[k].re + (double)xl[k].re, x[k].im + (double)xl[k].im);
+      rv[k] = cx(fma(k2, acc[k].re, bh[k].re - x[k].re), fma(k2, acc[k].im, bh[k].im - x[k].im));
+      n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
+      zero[k] = cx((typename Spin<SPA>::R)0, (typename Spin<SPA>::R)0);
+    }
+    nrm = n;
+    Spin<P64>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
+    Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, zero);
+    Spin<P64>::store(slot_wptr(S, S_RT, r, par), S.vh, s, rv);
+    Cx<typename Spin<SPL>::R> lo[12];
+    convert12(rv, lo);
+    Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, lo);
+  }
+};
+
+// Full-lattice residual rt = b - (x - kappa*acc) on the output parity (with
+// acc = H x this is b - D x; with acc = Hdag x it is b - D^dag x),
+// optionally also r_low <- rt.  Reduction |rt|^2.
+template <int SPL, bool STORE_LOW>
+struct EpiResidFull {
+  static constexpr bool kReduce = true;
+  int gate;
+  int slot_rt;  // < 0: norm only
+  int slot_x;
+  int slot_b;
+  __host__ double io_bytes() const {
+    return 2.0 * Spin<P64>::kBytes + (slot_rt >= 0 ? Spin<P64>::kBytes : 0) + (STORE_LOW ? Spin<SPL>::kBytes : 0);
+  }
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<double> (&acc)[12],
+                                        double& nrm) const {
+    Cx<double> x[12], b[12], rv[12];
+    Spin<P64>::load(slot_ptr(S, slot_x, r, par), S.vh, s, x);
+    Spin<P64>::load(slot_ptr(S, slot_b, r, par), S.vh, s, b);
+    double n = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      rv[k] = cx(fma(S.kappa, acc[k].re, b[k].re - x[k].re), fma(S.kappa, acc[k].im, b[k].im - x[k].im));
+      n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
+    }
+    nrm = n;
+    if (slot_rt >= 0) Spin<P64>::store(slot_wptr(S, slot_rt, r, par), S.vh, s, rv);
+    if (STORE_LOW) {
+      Cx<typename Spin<SPL>::R> lo[12];
+      convert12(rv, lo);
+      Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, lo);
+    }
+  }
+};
+
+// ------------------------------------------------------------------ block prologue
+// System descriptor into shared memory, the gate of every column of the
+// system, this thread's site s on output parity par and right-hand side r.
+// A block returns at once only when every column of its system is gated off:
+// all blocks of a system read the same gates (they change only in the
+// system's last block, after every block has read them), so either all of a
+// system's blocks arrive at the reduction or none does.
+#define DW_BLOCK_PROLOGUE(GATE)                                            \
+  __shared__ SysDesc S;                                                    \
+  __shared__ int act[64];                                                  \
+  const int T = B.T, RB = B.RB;                                            \
+  int b = blockIdx.x, par;                                                 \
+  if (par_mode == 2) {                                                     \
+    par = b >= B.ntot ? 1 : 0;                                             \
+    b -= par * B.ntot;                                                     \
+  } else {                                                                 \
+    par = par_mode;                                                        \
+  }                                                                        \
+  load_desc(S, B.sd, block_system(B, b));                                  \
+  __syncthreads();                                                         \
+  for (int i_ = threadIdx.x; i_ < S.nrhs; i_ += blockDim.x)                \
+    act[i_] = gate_of(GATE, ra.cols, S.col0 + i_);                         \
+  __syncthreads();                                                         \
+  int any = 0;                                                             \
+  for (int i_ = 0; i_ < S.nrhs; ++i_) any |= act[i_];                      \
+  if (!any) return;                                                        \
+  const int rl = threadIdx.x / T;                                          \
+  const int r = blockIdx.y * RB + rl;                                      \
+  const int tile = b - S.tile0;                                            \
+  const int s = tile * T + (threadIdx.x - rl * T);                         \
+  const bool valid = s < S.vh && r < S.nrhs && act[r < S.nrhs ? r : 0];
+
+#define DW_BLOCK_REDUCE(val)                                               \
+  {                                                                        \
+    const int ntiles = par_mode == 2 ? 2 * S.tpp : S.tpp;                  \
+    const int tt = par_mode == 2 ? par * S.tpp + tile : tile;              \
+    reduce_finalize(S, T, RB, tt, ntiles, val, ra);                        \
+  }
+
+// ------------------------------------------------------------------ the stencil kernel
+// par_mode 0/1: output parity fixed, grid = ntot blocks.  par_mode 2: both
+// parities, grid = 2*ntot (block b >= ntot works on odd output sites).
+// Input is read on the opposite parity.  SPA: arithmetic-precision tag.
+template <int SPA, int LP, bool C12, bool DAG, class In, class Epi>
+__global__ void __launch_bounds__(256) k_hop(const __grid_constant__ Batch B, int par_mode, int link_slot, In in,
+                                             Epi epi, RedArgs ra) {
+  using R = typename Spin<SPA>::R;
+  DW_BLOCK_PROLOGUE(epi.gate)
+  double nrm = 0.0;
+  if (valid) {
+    const Coord c = coord_of(S, s, par);
+    const int pin = par ^ 1;
+    const char* ulink_own = slot_ptr(S, link_slot, 0, par);  // links based at this site
+    const char* ulink_nb = slot_ptr(S, link_slot, 0, pin);   // links based at the neighbour
+    const long long mu_stride = (long long)Link<LP, C12>::kBytes * S.vh;
+    constexpr int SF = DAG ? +1 : -1;  // forward projector sign
+    constexpr int SB = -SF;            // backward projector sign
+    Cx<R> acc[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc[k] = cx((R)0, (R)0);
+
+#define DW_HOP_DIR(MU)                                                          \
+  {                                                                             \
+    float eta;                                                                  \
+    Cx<R> p[12], h[6], g[6], u[9];                                              \
+    const int nf = neighbour<MU, +1>(S, c, s, &eta);                            \
+    in.load(S, pin, r, nf, p);                                                  \
+    project<MU, SF>(p, h);                                                      \
+    Link<LP, C12>::load(ulink_own + MU * mu_stride, S.vh, s, u);                 \
+    if (eta < 0.f) {                                                            \
+      _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im); \
+    }                                                                           \
+    su3_mul<false>(u, h, g);                                                    \
+    accumulate<MU, SF>(acc, g);                                                 \
+    const int nb = neighbour<MU, -1>(S, c, s, &eta);                            \
+    in.load(S, pin, r, nb, p);                                                  \
+    project<MU, SB>(p, h);                                                      \
+    Link<LP, C12>::load(ulink_nb + MU * mu_stride, S.vh, nb, u);                 \
+    if (eta < 0.f) {                                                            \
+      _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im); \
+    }                                                                           \
+    su3_mul<true>(u, h, g);                                                     \
+    accumulate<MU, SB>(acc, g);                                                 \
+  }
+    DW_HOP_DIR(0)
+    DW_HOP_DIR(1)
+    DW_HOP_DIR(2)
+    DW_HOP_DIR(3)
+#undef DW_HOP_DIR
+    epi.write(S, par, r, s, acc, nrm);
+  }
+  if (Epi::kReduce) DW_BLOCK_REDUCE(nrm)
+}
+
+// ------------------------------------------------------------------ site-local kernels
+// xl += alpha p;  r -= alpha w;  reduction |r|^2 -> FIN_UPDATE
+template <int SPL, int SPA>
+__global__ void __launch_bounds__(256) k_update_xr(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
+  DW_BLOCK_PROLOGUE(G_ACTIVE)
+  double nrm = 0.0;
+  if (valid) {
+    using RL = typename Spin<SPL>::R;
+    using RA = typename Spin<SPA>::R;
+    const double alpha = ra.cols[S.col0 + r].alpha;
+    Cx<RL> p[12], w[12], rv[12];
+    Cx<RA> xl[12];
+    Spin<SPL>::load(slot_ptr(S, S_P, r, par), S.vh, s, p);
+    Spin<SPL>::load(slot_ptr(S, S_W, r, par), S.vh, s, w);
+    Spin<SPL>::load(slot_ptr(S, S_R, r, par), S.vh, s, rv);
+    Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
+    const RL a = (RL)alpha;
+    const RA aa = (RA)alpha;
+    RL n = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      xl[k] = cx(fma(aa, (RA)p[k].re, xl[k].re), fma(aa, (RA)p[k].im, xl[k].im));
+      rv[k] = cx(fma(-a, w[k].re, rv[k].re), fma(-a, w[k].im, rv[k].im));
+    }
+    Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, xl);
+    // the norm is taken of the value as stored, so the recursion sees what
+    // the next kernels will read
+    Spin<SPL>::roundtrip(rv);
+    Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, rv);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
+    nrm = (double)n;
+  }
+  ra.fin = FIN_UPDATE;
+  DW_BLOCK_REDUCE(nrm)
+}
+
+// p = z + beta p
+template <int SPL>
+__global__ void __launch_bounds__(256) k_update_p(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
+  DW_BLOCK_PROLOGUE(G_ACTIVE)
+  if (valid) {
+    using RL = typename Spin<SPL>::R;
+    const RL beta = (RL)ra.cols[S.col0 + r].beta;
+    Cx<RL> p[12], z[12];
+    Spin<SPL>::load(slot_ptr(S, S_P, r, par), S.vh, s, p);
+    Spin<SPL>::load(slot_ptr(S, S_Z, r, par), S.vh, s, z);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) p[k] = cx(fma(beta, p[k].re, z[k].re), fma(beta, p[k].im, z[k].im));
+    Spin<SPL>::store(slot_wptr(S, S_P, r, par), S.vh, s, p);
+  }
+}
+
+// x += xl; xl = 0   (full-lattice reliable update, both parities)
+template <int SPA>
+__global__ void __launch_bounds__(256) k_fold_x(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
+  DW_BLOCK_PROLOGUE(G_REL)
+  if (valid) {
+    using RA = typename Spin<SPA>::R;
+    Cx<double> x[12];
+    Cx<RA> xl[12];
+    Spin<P64>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
+    Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      x[k] = cx(x[k].re + (double)xl[k].re, x[k].im + (double)xl[k].im);
+      xl[k] = cx((RA)0, (RA)0);
+    }
+    Spin<P64>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
+    Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, xl);
+  }
+}
+
+// |field|^2 of slot over the launched parities -> finalizer ra.fin (gate: all)
+template <int SP>
+__global__ void __launch_bounds__(256) k_norm(const __grid_constant__ Batch B, int par_mode, int slot, RedArgs ra) {
+  DW_BLOCK_PROLOGUE(G_ALL)
+  double nrm = 0.0;
+  if (valid) {
+    Cx<typename Spin<SP>::R> v[12];
+    Spin<SP>::load(slot_ptr(S, slot, r, par), S.vh, s, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) nrm = fma((double)v[k].re, (double)v[k].re, fma((double)v[k].im, (double)v[k].im, nrm));
+  }
+  DW_BLOCK_REDUCE(nrm)
+}
+
+// dst = convert(src), over the launched parities (gate: all)
+template <int SPD, int SPS>
+__global__ void __launch_bounds__(256) k_convert(const __grid_constant__ Batch B, int par_mode, int slot_dst, int slot_src,
+                                                 RedArgs ra) {
+  DW_BLOCK_PROLOGUE(G_ALL)
+  if (valid) {
+    Cx<typename Spin<SPS>::R> v[12];
+    Cx<typename Spin<SPD>::R> o[12];
+    Spin<SPS>::load(slot_ptr(S, slot_src, r, par), S.vh, s, v);
+    convert12(v, o);
+    Spin<SPD>::store(slot_wptr(S, slot_dst, r, par), S.vh, s, o);
+  }
+}
+
+}  // namespace dw

@@ -1,0 +1,111 @@
+// dw_solver.cu -- C ABI of the solvers: argument checks and precision dispatch.
+#include "dw_solver.cuh"
+
+namespace dw {
+
+extern template struct CG<P64, P64, false>;
+extern template struct CG<P32, P32, false>;
+extern template struct CG<P32, P32, true>;
+extern template struct CG<P16, P32, false>;
+extern template struct CG<P16, P32, true>;
+extern template struct CG<PB16, P32, false>;
+extern template struct CG<PB16, P32, true>;
+
+static dw_status dispatch(const SolveArgs& a) {
+  const bool c = a.p.compress12 != 0;
+  switch (a.p.inner) {
+    case DW_F64: return CG<P64, P64, false>::run(a);
+    case DW_F32: return c ? CG<P32, P32, true>::run(a) : CG<P32, P32, false>::run(a);
+    case DW_F16: return c ? CG<P16, P32, true>::run(a) : CG<P16, P32, false>::run(a);
+    case DW_BF16: return c ? CG<PB16, P32, true>::run(a) : CG<PB16, P32, false>::run(a);
+  }
+  return set_error(DW_ERR_PRECISION, "unknown inner precision %d", (int)a.p.inner);
+}
+
+static dw_status check_params(const dw_solver_params* p) {
+  DW_CHECK(p != nullptr, DW_ERR_ARG, "params is NULL");
+  DW_CHECK(p->tol > 0 && p->tol < 1, DW_ERR_ARG, "tol %g must lie in (0, 1)", p->tol);
+  DW_CHECK(p->maxiter > 0, DW_ERR_ARG, "maxiter must be positive");
+  DW_CHECK(p->inner >= DW_F64 && p->inner <= DW_BF16, DW_ERR_PRECISION, "unknown inner precision");
+  DW_CHECK(p->inner == DW_F64 || (p->delta > 0 && p->delta < 1), DW_ERR_ARG, "delta %g must lie in (0, 1)",
+           p->delta);
+  DW_CHECK(p->tile == 0 || (p->tile >= 32 && p->tile <= 256 && p->tile % 32 == 0), DW_ERR_ARG,
+           "tile %d must be 0 or a multiple of 32 in [32, 256]", p->tile);
+  DW_CHECK(p->check_every >= 0 && p->timeout_s >= 0, DW_ERR_ARG, "negative check_every / timeout");
+  return DW_OK;
+}
+
+static dw_status check_system(const dw_field* U, const dw_field* b, const dw_field* x, int nrhs) {
+  DW_CHECK(U && b && x, DW_ERR_ARG, "NULL field");
+  DW_CHECK(U->kind == DW_GAUGE && U->prec == DW_F64 && !U->compress12, DW_ERR_PRECISION,
+           "solvers take an FP64 18-real gauge field");
+  DW_CHECK(b->kind == DW_SPINOR_FULL && x->kind == DW_SPINOR_FULL, DW_ERR_SHAPE, "b and x must be FULL spinors");
+  DW_CHECK(b->prec == DW_F64 && x->prec == DW_F64, DW_ERR_PRECISION, "b and x must be FP64");
+  DW_CHECK(same_dims(U->lat, b->lat) && same_dims(U->lat, x->lat), DW_ERR_SHAPE, "lattice dimensions differ");
+  DW_CHECK(b->nrhs == nrhs && x->nrhs == nrhs, DW_ERR_SHAPE, "every b and x must have nrhs = %d", nrhs);
+  DW_CHECK(b->ptr != x->ptr, DW_ERR_ARG, "b and x must not alias");
+  return DW_OK;
+}
+
+dw_status solve_many(int n, const dw_field* const* U, const dw_field* const* b, dw_field* const* x,
+                     const dw_solver_params* p, dw_solver_stats* stats, cudaStream_t st, int mode) {
+  DW_CHECK(n >= 1 && U && b && x, DW_ERR_ARG, "need n >= 1 systems and non-NULL arrays");
+  DW_TRY(check_params(p));
+  const int nrhs = b[0] ? b[0]->nrhs : 0;
+  for (int i = 0; i < n; ++i) DW_TRY(check_system(U[i], b[i], x[i], nrhs));
+  dw_status worst = DW_OK;
+  for (int g = 0; g < n; g += kMaxSys) {
+    SolveArgs a;
+    a.n = n - g < kMaxSys ? n - g : kMaxSys;
+    a.U = const_cast<dw_field* const*>(U + g);
+    a.b = b + g;
+    a.x = x + g;
+    a.p = *p;
+    if (mode == MODE_EO && !p->eo) mode = MODE_FULL;
+    a.mode = mode;
+    a.stats = stats ? stats + (size_t)g * nrhs : nullptr;
+    a.st = st;
+    dw_status s = dispatch(a);
+    if (s != DW_OK && worst == DW_OK) worst = s;
+    if (s != DW_OK && s != DW_ERR_NOT_CONVERGED && s != DW_ERR_BREAKDOWN && s != DW_ERR_TIMEOUT) return s;
+  }
+  return worst;
+}
+
+}  // namespace dw
+
+using namespace dw;
+
+extern "C" {
+
+dw_status dw_solver_params_default(dw_solver_params* p) {
+  DW_CHECK(p != nullptr, DW_ERR_ARG, "params is NULL");
+  p->tol = 1e-10;
+  p->maxiter = 20000;
+  p->inner = DW_F32;
+  p->delta = 0.1;
+  p->eo = 1;
+  p->compress12 = 0;
+  p->recompute_fwd = 1;
+  p->tile = 0;
+  p->check_every = 0;
+  p->timeout_s = 0;
+  return DW_OK;
+}
+
+dw_status dw_cg_solve(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
+                      dw_solver_stats* stats, dw_stream_t stream) {
+  return solve_many(1, &U, &b, &x, p, stats, reinterpret_cast<cudaStream_t>(stream), MODE_EO);
+}
+
+dw_status dw_cg_solve_batched(int n, const dw_field* const* U, const dw_field* const* b, dw_field* const* x,
+                              const dw_solver_params* p, dw_solver_stats* stats, dw_stream_t stream) {
+  return solve_many(n, U, b, x, p, stats, reinterpret_cast<cudaStream_t>(stream), MODE_EO);
+}
+
+dw_status dw_cg_solve_normal(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
+                             dw_solver_stats* stats, dw_stream_t stream) {
+  return solve_many(1, &U, &b, &x, p, stats, reinterpret_cast<cudaStream_t>(stream), MODE_NORMAL);
+}
+
+}  // extern "C"

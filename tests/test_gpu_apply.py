@@ -1,0 +1,156 @@
+"""GPU operator parity: dw_apply / dw_apply_dag / dw_normal_apply through the
+C ABI against the FP64 oracle on the same seeded inputs.
+
+Bars: FP64 storage <= 1e-13 and FP32 <= 1e-6 per-site relative norm;
+16-bit storage (FP16 / BF16 with FP32 arithmetic) is held to bounds derived
+from the unit roundoff of the storage type (2^-11 for FP16 values scaled to
+[-1, 1] per site, 2^-8 for BF16) times the few roundings on the path.
+Lattices are chosen so that half volumes span several thread blocks and end
+in a partial block (192, 960 and 1620 sites per parity with 128-site blocks).
+"""
+import numpy as np
+import pytest
+
+from helpers import parity_of_sites, site_err
+from oracle import oracle as O
+from paper_2001_05218_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f64": 1e-13, "f32": 1e-6, "f16": 4e-3, "bf16": 3e-2}
+DIMS = [(4, 4, 4, 6), (8, 6, 4, 10), (6, 10, 6, 6)]
+
+
+@pytest.fixture(scope="module")
+def dw():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2001_05218_gb300 import dw as m
+    return m
+
+
+def _setup(dims, seed=101, kind="haar"):
+    U = I.gauge_field(dims, kind, seed, 1, 0.5)
+    psi = I.gaussian_spinor(dims, seed, 2)
+    return U, psi
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("anti_t", [1, 0])
+def test_apply_full_f64(dw, dims, anti_t):
+    kappa = 0.1234
+    U, psi = _setup(dims)
+    Ug = dw.gauge(dims, kappa, U, t_antiperiodic=anti_t)
+    x = dw.spinor(dims, psi)
+    out = dw.spinor(dims)
+    for dag in (False, True):
+        dw.apply(Ug, x, out, dag=dag)
+        ref = O.dirac(dims, kappa, U, psi, anti_t=anti_t, dag=dag)
+        assert site_err(out.download(), ref) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("dims", DIMS[:2])
+@pytest.mark.parametrize("prec,c12", [("f64", 0), ("f64", 1), ("f32", 0), ("f32", 1), ("f16", 0), ("f16", 1),
+                                      ("bf16", 0), ("bf16", 1)])
+def test_apply_precisions(dw, dims, prec, c12):
+    kappa = 0.118
+    U, psi = _setup(dims, 7)
+    P = dw.PREC[prec]
+    Ug = dw.gauge(dims, kappa, U, prec=P, compress12=c12)
+    x = dw.spinor(dims, psi, prec=P)
+    out = dw.spinor(dims, prec=P)
+    for dag in (False, True):
+        dw.apply(Ug, x, out, dag=dag)
+        ref = O.dirac(dims, kappa, U, psi, dag=dag)
+        e = site_err(out.download(), ref)
+        assert e <= TOL[prec], (prec, c12, dag, e)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("parity", [0, 1])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_apply_schur(dw, dims, parity, prec):
+    kappa = 0.125
+    U, psi = _setup(dims, 17)
+    par = parity_of_sites(dims)
+    P = dw.PREC[prec]
+    kind = dw.DW_SPINOR_EVEN if parity == 0 else dw.DW_SPINOR_ODD
+    Ug = dw.gauge(dims, kappa, U, prec=P)
+    sub = psi[par == parity]
+    x = dw.spinor(dims, sub, kind=kind, prec=P)
+    out = dw.spinor(dims, kind=kind, prec=P)
+    full = np.zeros_like(psi)
+    full[par == parity] = sub
+    for dag in (False, True):
+        dw.apply(Ug, x, out, dag=dag)
+        ref = O.schur(dims, kappa, U, full, parity=parity, dag=dag)[par == parity]
+        assert site_err(out.download(), ref) <= TOL[prec]
+    dw.apply(Ug, x, out, normal=True)
+    t = O.schur(dims, kappa, U, full, parity=parity)
+    ref = O.schur(dims, kappa, U, t, parity=parity, dag=True)[par == parity]
+    assert site_err(out.download(), ref) <= 10 * TOL[prec]
+
+
+def test_normal_apply_full(dw):
+    dims, kappa = (4, 4, 4, 6), 0.11
+    U, psi = _setup(dims, 23)
+    Ug = dw.gauge(dims, kappa, U)
+    x = dw.spinor(dims, psi)
+    out = dw.spinor(dims)
+    dw.apply(Ug, x, out, normal=True)
+    assert site_err(out.download(), O.normal(dims, kappa, U, psi)) <= 1e-13
+
+
+def test_multi_rhs_apply(dw):
+    dims, kappa, n = (8, 6, 4, 10), 0.12, 5
+    U, _ = _setup(dims, 29)
+    psis = np.stack([I.gaussian_spinor(dims, 29, 10 + r) for r in range(n)])
+    Ug = dw.gauge(dims, kappa, U, prec=dw.DW_F32)
+    x = dw.spinor(dims, psis, prec=dw.DW_F32, nrhs=n)
+    out = dw.spinor(dims, prec=dw.DW_F32, nrhs=n)
+    dw.apply(Ug, x, out)
+    got = out.download()
+    for r in range(n):
+        assert site_err(got[r], O.dirac(dims, kappa, U, psis[r])) <= TOL["f32"]
+
+
+def test_layout_roundtrip_is_exact(dw):
+    dims = (6, 10, 6, 6)
+    U, psi = _setup(dims, 31)
+    par = parity_of_sites(dims)
+    assert np.array_equal(dw.spinor(dims, psi).download(), psi)
+    assert np.array_equal(dw.spinor(dims, psi[par == 1], kind=dw.DW_SPINOR_ODD).download(), psi[par == 1])
+    g = dw.gauge(dims, 0.1, U)
+    lat = g.lat
+    assert np.array_equal(g.download(), U)
+    g12 = dw.gauge(dims, 0.1, U, compress12=1)
+    assert np.abs(g12.download() - U).max() < 1e-14  # row 2 rebuilt from SU(3) unitarity
+
+
+def test_golden_fixture_on_gpu(dw):
+    import os
+    from test_golden_and_inputs import load_golden
+    meta, Dpsi, Ddag, _ = load_golden()
+    dims, kappa, seed = meta["dims"], meta["kappa"], meta["seed"]
+    U = I.gauge_field(dims, "haar", seed, 1)
+    psi = I.gaussian_spinor(dims, seed, 2)
+    Ug = dw.gauge(dims, kappa, U)
+    x = dw.spinor(dims, psi)
+    out = dw.spinor(dims)
+    dw.apply(Ug, x, out)
+    assert site_err(out.download(), Dpsi) <= 1e-13
+    dw.apply(Ug, x, out, dag=True)
+    assert site_err(out.download(), Ddag) <= 1e-13
+
+
+def test_apply_rejects_mismatches(dw):
+    dims = (4, 4, 4, 6)
+    U, psi = _setup(dims)
+    Ug = dw.gauge(dims, 0.1, U)
+    x = dw.spinor(dims, psi)
+    y32 = dw.spinor(dims, prec=dw.DW_F32)
+    assert dw.dw_apply(Ug.handle, x.handle, y32.handle, dw.current_stream()) == dw.DW_ERR_SHAPE or \
+        dw.dw_apply(Ug.handle, x.handle, y32.handle, dw.current_stream()) == dw.DW_ERR_PRECISION
+    other = dw.spinor((4, 4, 4, 8))
+    assert dw.dw_apply(Ug.handle, x.handle, other.handle, dw.current_stream()) == dw.DW_ERR_SHAPE
+    assert dw.dw_apply(Ug.handle, x.handle, x.handle, dw.current_stream()) == dw.DW_ERR_ARG
