@@ -150,8 +150,11 @@ typedef struct {
   int compress12;      /* inner-precision links stored as 12 reals */
   int recompute_fwd;   /* dw_cg_backward: 1 = recompute the forward solution */
   int tile;            /* sites per thread block (0 = library choice) */
-  int check_every;     /* iterations per convergence poll (0 = library choice) */
+  int check_every;     /* host-stepped loop only: iterations per convergence poll
+                          (0 = library choice); the default loop runs on the device */
   double timeout_s;    /* device-side time budget per solve (0 = none) */
+  int verify_normal;   /* 1: also compute normal_rel_resid (two more FP64 operator
+                          applications); 0: normal_rel_resid = -1 */
 } dw_solver_params;
 
 typedef struct {
@@ -166,7 +169,13 @@ typedef struct {
 } dw_solver_stats;
 
 /* Fill *p with defaults: tol 1e-10, maxiter 20000, inner DW_F32, delta 0.1,
- * eo 1, compress12 0, recompute_fwd 1, tile 0, check_every 0, timeout 0. */
+ * eo 1, compress12 0, recompute_fwd 1, tile 0, check_every 0, timeout 0,
+ * verify_normal 0.
+ * The CG loop runs as one CUDA graph: a device-side while-loop over the
+ * iteration, with the FP64 reliable update in a conditional node; the host
+ * waits once per solve.  While dw_profile_start is active the loop is stepped
+ * from the host instead (one poll per iteration) so that every stencil launch
+ * can be timed with events; the arithmetic is identical. */
 dw_status dw_solver_params_default(dw_solver_params* p);
 
 /* Solve D x = b by CG on the normal equations D^dag D x = D^dag b (with the
@@ -211,12 +220,14 @@ dw_status dw_cg_backward(const dw_field* U, const dw_field* phi_or_b, const dw_f
 
 /* Launch accounting for measurement (no counterpart in the paper, whose
  * Fig. 2 is a simulated timeline).  Between start and stop every kernel
- * launch of the library is counted, and every stencil launch is bracketed by
- * two CUDA events on its own stream.  Entries aggregate the stencil launches
- * by (arithmetic precision / link storage): launches, summed event time,
- * algorithmic bytes (links 8 per site once per site, each spinor touched
- * once) and model flops (1320 per output site).  stop synchronises the
- * device; while active it adds two event records per stencil launch. */
+ * executed by the library is counted (kernels inside the solver's CUDA graph
+ * from the device loop counters).  With time_stencils != 0 every stencil
+ * launch is also bracketed by two CUDA events on its own stream, and solvers
+ * step their loop from the host (events cannot live inside conditional graph
+ * nodes).  Entries aggregate the timed stencil launches by (arithmetic
+ * precision / link storage): launches, summed event time, algorithmic bytes
+ * (8 links per output site, each spinor touched once) and model flops (1320
+ * per output site).  stop synchronises the device. */
 typedef struct {
   char name[64];
   long long launches;
@@ -225,7 +236,7 @@ typedef struct {
   double flops;
 } dw_profile_entry;
 
-dw_status dw_profile_start(void);
+dw_status dw_profile_start(int time_stencils);
 dw_status dw_profile_stop(dw_profile_entry* entries, int max_entries, int* n_entries, long long* launches);
 
 /* ------------------------------------------------------------------- misc */

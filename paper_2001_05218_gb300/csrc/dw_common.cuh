@@ -405,13 +405,18 @@ struct ColState {
   int active;      // 1 while iterating
   int do_rel;      // reliable update pending
   int status;      // dw_status of this column
-  int pad[2];
+  int xzero;       // initial guess is zero: the first residual is the source itself
+  int pad;
 };
 
 // Batch-wide flags.
 struct Flags {
-  int active;      // number of active columns
-  int err;         // first device error code (0 = none)
+  int active;       // number of active columns
+  int rel_pending;  // number of columns with a reliable update pending
+  int loops;        // iterations run by the device-driven loop
+  int max_loops;    // hard cap on loops (maxiter + 2)
+  int rel_runs;     // reliable-update passes run by the device-driven loop
+  int pad;
 };
 
 enum Fin {
@@ -425,6 +430,8 @@ enum Fin {
   FIN_RELIABLE,    // rr = rr_ref = v (true residual); convergence decision
   FIN_GAMMA0,      // gamma = v, beta = 0
   FIN_BETA,        // beta = v / gamma; gamma = v
+  FIN_XNORM,       // |x0|^2: a zero guess skips the first FP64 residual
+  FIN_RESID0,      // first residual = source (zero guess)
 };
 
 struct RedArgs {
@@ -476,12 +483,29 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
         deactivate(C, ra.flags, 7);
       } else if (v <= C.tol2 || v < C.delta2 * C.rr_ref || C.iter >= C.maxiter || timeout) {
         C.do_rel = 1;
+        atomicAdd(&ra.flags->rel_pending, 1);
       }
       break;
     }
+    case FIN_XNORM:
+      C.xzero = v == 0.0 ? 1 : 0;
+      if (C.xzero && C.do_rel) {
+        C.do_rel = 0;
+        atomicSub(&ra.flags->rel_pending, 1);
+      }
+      break;
+    case FIN_RESID0:
+      if (!C.xzero) break;
+      C.xzero = 0;
+      C.rr = v;
+      C.rr_ref = v;
+      if (v <= C.tol2) deactivate(C, ra.flags, 0);
+      else if (!isfinite(v)) deactivate(C, ra.flags, 7);
+      break;
     case FIN_RELIABLE: {
       if (!C.do_rel) break;
       C.do_rel = 0;
+      atomicSub(&ra.flags->rel_pending, 1);
       C.rr = v;
       C.rr_ref = v;
       C.nrel += 1;

@@ -12,7 +12,8 @@ namespace dw {
 // kernel launch and brackets each stencil launch with CUDA events on its
 // stream, with the launch's algorithmic bytes and model flops.
 struct Profiler {
-  bool on = false;
+  bool on = false;      // count launches
+  bool timing = false;  // also bracket stencil launches with events
   long long launches = 0;
   struct Rec {
     int cat;
@@ -65,15 +66,15 @@ template <int SPA, int LP, bool C12, bool DAG, class In, class Epi>
 inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int fin = FIN_STORE0) {
   Profiler& pr = profiler();
   cudaEvent_t ea = nullptr, eb = nullptr;
-  if (pr.on) {
-    pr.launches += 1;
+  if (pr.on) pr.launches += 1;
+  if (pr.timing) {
     ea = pr.event();
     eb = pr.event();
     cudaEventRecord(ea, E.st);
   }
   k_hop<SPA, LP, C12, DAG, In, Epi><<<E.grid(par_mode), E.P.block, 0, E.st>>>(E.P.B, par_mode, link_slot, in, epi,
                                                                               E.ra(fin));
-  if (pr.on) {
+  if (pr.timing) {
     cudaEventRecord(eb, E.st);
     const int npar = par_mode == 2 ? 2 : 1;
     double bytes = 0, sites = 0;

@@ -356,9 +356,10 @@ extern "C" {
 
 const char* dw_last_error(void) { return g_err; }
 
-dw_status dw_profile_start(void) {
+dw_status dw_profile_start(int time_stencils) {
   Profiler& p = profiler();
   p.on = true;
+  p.timing = time_stencils != 0;
   p.launches = 0;
   p.recs.clear();
   p.next = 0;
@@ -391,6 +392,7 @@ dw_status dw_profile_stop(dw_profile_entry* out, int max_entries, int* n_entries
   if (n_entries) *n_entries = n;
   if (launches) *launches = p.launches;
   p.on = false;
+  p.timing = false;
   p.recs.clear();
   p.next = 0;
   return DW_OK;

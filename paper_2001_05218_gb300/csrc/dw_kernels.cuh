@@ -23,7 +23,7 @@
 namespace dw {
 
 enum Coef { C_ONE = 0, C_MK, C_PK, C_MK2, C_PK2 };
-enum Gate { G_ACTIVE = 0, G_REL, G_ALL };
+enum Gate { G_ACTIVE = 0, G_REL, G_ALL, G_XZERO };
 
 template <int C>
 __device__ __forceinline__ double coef_of(double kappa) {
@@ -32,6 +32,7 @@ __device__ __forceinline__ double coef_of(double kappa) {
 
 __device__ __forceinline__ int gate_of(int g, const ColState* cols, int col) {
   if (g == G_ALL) return 1;
+  if (g == G_XZERO) return cols[col].xzero;
   return g == G_ACTIVE ? cols[col].active : cols[col].do_rel;
 }
 
@@ -463,6 +464,23 @@ __global__ void __launch_bounds__(256) k_update_p(const __grid_constant__ Batch 
     for (int k = 0; k < 12; ++k) p[k] = cx(fma(beta, p[k].re, z[k].re), fma(beta, p[k].im, z[k].im));
     Spin<SPL>::store(slot_wptr(S, S_P, r, par), S.vh, s, p);
   }
+}
+
+// First residual for a zero initial guess: r_low = src, reduction |src|^2 -> FIN_RESID0
+template <int SPL>
+__global__ void __launch_bounds__(256) k_init_r(const __grid_constant__ Batch B, int par_mode, int slot_src, RedArgs ra) {
+  DW_BLOCK_PROLOGUE(G_XZERO)
+  double nrm = 0.0;
+  if (valid) {
+    Cx<double> v[12];
+    Cx<typename Spin<SPL>::R> lo[12];
+    Spin<P64>::load(slot_ptr(S, slot_src, r, par), S.vh, s, v);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) nrm = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, nrm));
+    convert12(v, lo);
+    Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, lo);
+  }
+  DW_BLOCK_REDUCE(nrm)
 }
 
 // x += xl; xl = 0   (full-lattice reliable update, both parities)

@@ -90,6 +90,7 @@ dw_status dw_solver_params_default(dw_solver_params* p) {
   p->tile = 0;
   p->check_every = 0;
   p->timeout_s = 0;
+  p->verify_normal = 0;
   return DW_OK;
 }
 

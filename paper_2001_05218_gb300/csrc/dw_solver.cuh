@@ -99,19 +99,135 @@ struct CG {
     }
   }
 
-  static void iteration(const Exec& E, int mode) {
-    const int pm = mode == MODE_EO ? 0 : 2;
+  static dw_status run(const SolveArgs& a);
+  static dw_status run_graph(const Exec& E, int mode, int* body_kernels, int* rel_kernels);
+  static dw_status run_stepped(const Exec& E, int mode, int maxiter);
+};
+
+// Condition setters for the device-driven loop (one thread).
+static __global__ void k_cond_rel(Flags* f, cudaGraphConditionalHandle h) {
+  const bool run = f->rel_pending > 0;
+  if (run) f->rel_runs += 1;
+  cudaGraphSetConditional(h, run ? 1u : 0u);
+}
+static __global__ void k_cond_loop(Flags* f, cudaGraphConditionalHandle h) {
+  const int loops = f->loops + 1;
+  f->loops = loops;
+  cudaGraphSetConditional(h, (f->active > 0 && loops < f->max_loops) ? 1u : 0u);
+}
+
+struct CaptureStreams {
+  cudaStream_t a = nullptr, b = nullptr;
+  CaptureStreams() {
+    cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking);
+    cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking);
+  }
+};
+
+// The whole CG loop as one graph: while (active columns) { iteration with the
+// reliable update in an if-node }.  Both conditions are set on the device,
+// the loop is capped at maxiter + 2 passes, and every column also leaves the
+// loop through its own maxiter / timeout / breakdown checks.
+template <int L, int A, bool C12>
+dw_status CG<L, A, C12>::run_graph(const Exec& E0, int mode, int* body_kernels, int* rel_kernels) {
+  static thread_local CaptureStreams cs;
+  const int pm = mode == MODE_EO ? 0 : 2;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  DW_CUDA(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle hw, hr;
+  DW_CUDA(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = hw;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wn;
+  DW_CUDA(cudaGraphAddNode(&wn, g, nullptr, nullptr, 0, &wp));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+  DW_CUDA(cudaGraphConditionalHandleCreate(&hr, body, 0, cudaGraphCondAssignDefault));
+
+  Exec E = E0;
+  E.st = cs.a;
+  Profiler& pr = profiler();
+  const long long c0 = pr.launches;
+  long long c1 = c0, c2 = c0;
+  DW_CUDA(cudaStreamBeginCaptureToGraph(cs.a, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  wstep(E, mode);
+  count_launch();
+  count_launch();
+  k_update_xr<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_UPDATE));
+  k_cond_rel<<<1, 1, 0, E.st>>>(E.rb.flags, hr);
+  {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t capg;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    DW_CUDA(cudaStreamGetCaptureInfo(cs.a, &cst, nullptr, &capg, &deps, nullptr, &ndeps));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hr;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t in;
+    DW_CUDA(cudaGraphAddNode(&in, capg, deps, nullptr, ndeps, &ip));
+    DW_CUDA(cudaStreamUpdateCaptureDependencies(cs.a, &in, nullptr, 1, cudaStreamSetCaptureDependencies));
+    Exec R = E;
+    R.st = cs.b;
+    c1 = pr.launches;
+    DW_CUDA(cudaStreamBeginCaptureToGraph(cs.b, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    reliable(R, mode);
+    cudaGraph_t tmp;
+    DW_CUDA(cudaStreamEndCapture(cs.b, &tmp));
+    c2 = pr.launches;
+  }
+  zstep(E, mode, FIN_BETA);
+  k_update_p<L><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_STORE0));
+  k_cond_loop<<<1, 1, 0, E.st>>>(E.rb.flags, hw);
+  count_launch();
+  count_launch();
+  cudaGraph_t tmp;
+  DW_CUDA(cudaStreamEndCapture(cs.a, &tmp));
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, E0.st);
+  if (ge) cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_error(e, "CG graph", __FILE__, __LINE__);
+  // kernel nodes per pass of the loop body and of the reliable-update branch;
+  // the executed counts are added once the device counters are read back
+  *body_kernels = (int)((c1 - c0) + (pr.launches - c2));
+  *rel_kernels = (int)(c2 - c1);
+  pr.launches = c0;
+  return DW_OK;
+}
+
+// Host-stepped loop: identical kernels, the host reads the device counters
+// after every update so that no launch is made without work; used while the
+// launch profiler is active.
+template <int L, int A, bool C12>
+dw_status CG<L, A, C12>::run_stepped(const Exec& E, int mode, int maxiter) {
+  static Flags* hf = nullptr;
+  if (!hf) DW_CUDA(cudaMallocHost((void**)&hf, sizeof(Flags)));
+  const int pm = mode == MODE_EO ? 0 : 2;
+  for (int it = 0; it < maxiter + 2; ++it) {
+    DW_CUDA(cudaMemcpyAsync(hf, E.rb.flags, sizeof(Flags), cudaMemcpyDeviceToHost, E.st));
+    DW_CUDA(cudaStreamSynchronize(E.st));
+    if (hf->active == 0) break;
     wstep(E, mode);
     count_launch();
     k_update_xr<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_UPDATE));
-    reliable(E, mode);
+    DW_CUDA(cudaMemcpyAsync(hf, E.rb.flags, sizeof(Flags), cudaMemcpyDeviceToHost, E.st));
+    DW_CUDA(cudaStreamSynchronize(E.st));
+    if (hf->rel_pending > 0) reliable(E, mode);
+    if (hf->active == 0) continue;
     zstep(E, mode, FIN_BETA);
     count_launch();
     k_update_p<L><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_STORE0));
   }
-
-  static dw_status run(const SolveArgs& a);
-};
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
 
 // Bytes of one even-odd spinor block in each role, per system and rhs.
 struct Arena {
@@ -198,12 +314,14 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
     c.delta2 = L == P64 ? 0.0 : a.p.delta * a.p.delta;
     c.maxiter = a.p.maxiter;
     c.active = 1;
-    c.do_rel = 1;  // the first FP64 residual is a "reliable update"
+    c.do_rel = 1;  // the first FP64 residual is a "reliable update" unless x0 = 0
     c.status = DW_ERR_NOT_CONVERGED;
   }
   Flags hf;
   hf.active = E.P.ncols;
-  hf.err = 0;
+  hf.rel_pending = E.P.ncols;
+  hf.loops = 0;
+  hf.max_loops = a.p.maxiter + 2;
   cudaEvent_t ev0, ev1;
   DW_CUDA(cudaEventCreate(&ev0));
   DW_CUDA(cudaEventCreate(&ev1));
@@ -211,12 +329,15 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
   DW_CUDA(cudaMemcpyAsync(E.rb.cols, hc.data(), sizeof(ColState) * hc.size(), cudaMemcpyHostToDevice, st));
   DW_CUDA(cudaMemcpyAsync(E.rb.flags, &hf, sizeof hf, cudaMemcpyHostToDevice, st));
   DW_CUDA(cudaMemsetAsync(E.rb.counter, 0, sizeof(int) * kMaxSys, st));
-  if (a.p.timeout_s > 0)
+  if (a.p.timeout_s > 0) {
+    count_launch();
     k_set_deadline<<<(E.P.ncols + 127) / 128, 128, 0, st>>>(E.rb.cols, E.P.ncols,
                                                            (unsigned long long)(a.p.timeout_s * 1e9));
+  }
 
   // ---- set-up
   norm<P64>(E, 2, S_B, FIN_BNORM);
+  norm<P64>(E, eo ? 0 : 2, S_X, FIN_XNORM);
   for (int i = 0; i < n; ++i) {
     const SysDesc& S = E.P.B.sd[i];
     for (auto pc : {S_XL, S_P}) {
@@ -228,33 +349,28 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
     // bh = b_e + kappa H_eo b_o
     hop<P64, P64, false, false>(E, 0, kLinkHi, InOne<P64>{S_B}, EpiXpay<P64, P64, C_PK, false>{S_BH, S_B, G_ALL});
   }
-  reliable(E, mode);                 // r = b - A x in FP64, r_low = r
-  zstep(E, mode, FIN_GAMMA0);        // z, gamma
+  if (mode != MODE_NORMAL) {
+    // zero guess: r = source (bh or b); otherwise r = source - A x in FP64
+    count_launch();
+    k_init_r<L><<<E.grid(eo ? 0 : 2), E.P.block, 0, st>>>(E.P.B, eo ? 0 : 2, eo ? S_BH : S_B, E.ra(FIN_RESID0));
+  } else {
+    count_launch();
+    k_init_r<L><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_B, E.ra(FIN_RESID0));
+  }
+  reliable(E, mode);
+  zstep(E, mode, FIN_GAMMA0);  // z, gamma
   count_launch();
   k_update_p<L><<<E.grid(eo ? 0 : 2), E.P.block, 0, st>>>(E.P.B, eo ? 0 : 2, E.ra(FIN_STORE0));  // p = z
   DW_CUDA(cudaGetLastError());
 
-  // ---- iterations: chunks of `chunk` iterations, host polls the active count
-  // one chunk behind so the GPU never waits for the host.
-  const int chunk = a.p.check_every > 0 ? a.p.check_every : 16;
-  static Flags* hflags = nullptr;  // pinned, two slots
-  if (!hflags) DW_CUDA(cudaMallocHost((void**)&hflags, 2 * sizeof(Flags)));
-  cudaEvent_t evc[2];
-  DW_CUDA(cudaEventCreateWithFlags(&evc[0], cudaEventDisableTiming));
-  DW_CUDA(cudaEventCreateWithFlags(&evc[1], cudaEventDisableTiming));
-  const long long max_chunks = (long long)a.p.maxiter / chunk + 3;
-  long long k = 0;
-  for (; k < max_chunks; ++k) {
-    for (int it = 0; it < chunk; ++it) iteration(E, mode);
-    DW_CUDA(cudaGetLastError());
-    DW_CUDA(cudaMemcpyAsync(&hflags[k & 1], E.rb.flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
-    DW_CUDA(cudaEventRecord(evc[k & 1], st));
-    if (k >= 1) {
-      DW_CUDA(cudaEventSynchronize(evc[(k - 1) & 1]));
-      if (hflags[(k - 1) & 1].active == 0) break;
-    }
+  // ---- iterations
+  int body_k = 0, rel_k = 0;
+  const bool graph = !profiler().timing;
+  if (graph) {
+    DW_TRY(run_graph(E, mode, &body_k, &rel_k));
+  } else {
+    DW_TRY(run_stepped(E, mode, a.p.maxiter));
   }
-  DW_CUDA(cudaEventSynchronize(evc[k & 1]));
 
   // ---- finish: odd sites, true residual, normal residual
   if (eo) {
@@ -263,10 +379,12 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
   if (mode != MODE_NORMAL) {
     hop<P64, P64, false, false>(E, 2, kLinkHi, InOne<P64>{S_X}, EpiResidFull<L, false>{G_ALL, S_RT, S_X, S_B},
                                 FIN_STORE0);
-    hop<P64, P64, false, true>(E, 2, kLinkHi, InOne<P64>{S_RT}, EpiXpay<P64, P64, C_MK, true>{-1, S_RT, G_ALL},
-                               FIN_STORE1);
-    hop<P64, P64, false, true>(E, 2, kLinkHi, InOne<P64>{S_B}, EpiXpay<P64, P64, C_MK, true>{-1, S_B, G_ALL},
-                               FIN_STORE2);
+    if (a.p.verify_normal) {
+      hop<P64, P64, false, true>(E, 2, kLinkHi, InOne<P64>{S_RT}, EpiXpay<P64, P64, C_MK, true>{-1, S_RT, G_ALL},
+                                 FIN_STORE1);
+      hop<P64, P64, false, true>(E, 2, kLinkHi, InOne<P64>{S_B}, EpiXpay<P64, P64, C_MK, true>{-1, S_B, G_ALL},
+                                 FIN_STORE2);
+    }
   } else {
     // |b - D^dag D x|^2
     hop<P64, P64, false, false>(E, 2, kLinkHi, InOne<P64>{S_X}, EpiXpay<P64, P64, C_MK, false>{S_AUX0, S_X, G_ALL});
@@ -275,14 +393,14 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
   }
   DW_CUDA(cudaEventRecord(ev1, st));
   DW_CUDA(cudaMemcpyAsync(hc.data(), E.rb.cols, sizeof(ColState) * hc.size(), cudaMemcpyDeviceToHost, st));
+  DW_CUDA(cudaMemcpyAsync(&hf, E.rb.flags, sizeof hf, cudaMemcpyDeviceToHost, st));
   cudaFreeAsync(arena, st);
   DW_CUDA(cudaStreamSynchronize(st));
+  if (graph && profiler().on) profiler().launches += (long long)hf.loops * body_k + (long long)hf.rel_runs * rel_k;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
-  cudaEventDestroy(evc[0]);
-  cudaEventDestroy(evc[1]);
   DW_CUDA(cudaGetLastError());
 
   // ---- statistics
@@ -302,7 +420,9 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
         o.iters = c.iter;
         o.reliable_updates = c.nrel > 0 ? c.nrel - 1 : 0;
         o.true_rel_resid = true_rel;
-        o.normal_rel_resid = mode == MODE_NORMAL ? true_rel : sqrt(c.store[1] / (c.store[2] > 0 ? c.store[2] : 1.0));
+        o.normal_rel_resid = mode == MODE_NORMAL ? true_rel
+                             : a.p.verify_normal ? sqrt(c.store[1] / (c.store[2] > 0 ? c.store[2] : 1.0))
+                                                 : -1.0;
         o.time_ms = ms;
         const double vh = (double)S.vh;
         const double hops_lo = (mode == MODE_EO ? 4.0 : 4.0) * c.iter;  // parity-hops per iteration

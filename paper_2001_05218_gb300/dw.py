@@ -41,7 +41,7 @@ class dw_solver_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner", ctypes.c_int),
                 ("delta", ctypes.c_double), ("eo", ctypes.c_int), ("compress12", ctypes.c_int),
                 ("recompute_fwd", ctypes.c_int), ("tile", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("timeout_s", ctypes.c_double)]
+                ("timeout_s", ctypes.c_double), ("verify_normal", ctypes.c_int)]
 
 
 class dw_profile_entry(ctypes.Structure):
@@ -80,7 +80,7 @@ _SIGS = {
     "dw_cg_solve_batched": [_I, ctypes.POINTER(_FP), ctypes.POINTER(_FP), ctypes.POINTER(_FP),
                             ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_solver_stats), _P],
     "dw_cg_solve_normal": [_FP, _FP, _FP, ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_solver_stats), _P],
-    "dw_profile_start": [],
+    "dw_profile_start": [_I],
     "dw_profile_stop": [ctypes.POINTER(dw_profile_entry), _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)],
     "dw_cg_backward": [_FP, _FP, _FP, _FP, _FP, _FP, _I, ctypes.POINTER(dw_solver_params),
                        ctypes.POINTER(dw_solver_stats), _P],
@@ -269,8 +269,8 @@ def cg_solve_batched(Us, bs, xs, p: dw_solver_params = None, raise_on_fail=True)
     return s, [st[i].as_dict() for i in range(n * nr)]
 
 
-def profile_start():
-    check(dw_profile_start())
+def profile_start(time_stencils=False):
+    check(dw_profile_start(1 if time_stencils else 0))
 
 
 def profile_stop():

@@ -172,6 +172,8 @@ WORKLOADS = {
     "wilson_32x32x32x64_exp0.6": dict(dims=(32, 32, 32, 64), kappa=0.1245, links="exp", amplitude=0.6, index=2),
     "wilson_24x24x24x48_exp0.4_12src": dict(dims=(24, 24, 24, 48), kappa=None, links="exp", amplitude=0.4, index=3),
     "wilson_16x16x16x32_exp0.4_grad": dict(dims=(16, 16, 16, 32), kappa=0.12, links="exp", amplitude=0.4, index=4),
+    # profiling size: stencil traffic above the 129 MB L2, ~1.5 GB on the device
+    "wilson_32x32x32x32_exp0.6": dict(dims=(32, 32, 32, 32), kappa=0.1245, links="exp", amplitude=0.6, index=5),
 }
 
 RAGGED_DIMS = [(8, 8, 8, 8), (8, 8, 8, 16), (12, 12, 12, 24), (16, 16, 16, 16),

@@ -29,10 +29,11 @@ def test_small_workload_full_lattice_fp64(dw):
     Ug = dw.gauge(dims, kappa, U)
     bg = dw.spinor(dims, b)
     x = dw.spinor(dims)
-    s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner=dw.DW_F64, eo=0))
+    s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner=dw.DW_F64, eo=0, verify_normal=1))
     xs = x.download()
     assert st[0]["true_rel_resid"] <= 1e-10
     assert _resid(dims, kappa, U, xs, b) <= 1e-10
+    assert 0 < st[0]["normal_rel_resid"] < 1e-8
     xo, it, rr = O.cgnr(dims, kappa, U, b, tol=1e-12)
     assert np.linalg.norm(xs - xo) / np.linalg.norm(xo) < 1e-7
     # plain FP64 CGNR on both sides with the same stopping rule: iteration
