@@ -138,6 +138,24 @@ dw_status dw_apply_dag(const dw_field* U, const dw_field* in, dw_field* out, dw_
 /* out = D^dag D in, or Dhat^dag Dhat in for parity fields. */
 dw_status dw_normal_apply(const dw_field* U, const dw_field* in, dw_field* out, dw_stream_t stream);
 
+/* dw_apply (dagger == 0) or dw_apply_dag (dagger != 0) without allocating any
+ * device memory.  The paper has no counterpart: this is for callers that
+ * cannot allocate GPU memory when they call -- code sharing the GPU with a
+ * framework whose caching allocator already holds nearly all of it, latency-
+ * critical loops where a cudaMalloc or cudaFree would synchronise the device,
+ * and code held to a fixed, planned memory budget.
+ * The Schur complement's intermediate parity field goes to one fixed 32 MiB
+ * array in device memory that the library reserves on every GPU that loads
+ * it, until the process exits.  Limit: nrhs * Vh * (bytes per site of the
+ * storage precision: 192 FP64, 96 FP32, 52 FP16/BF16) <= 32 MiB; larger
+ * fields return DW_ERR_SHAPE with nothing enqueued (FULL fields need no
+ * scratch).  All calls on a device share the array, which keeps the last
+ * call's contents; calls whose kernels can run at the same time on the GPU
+ * (e.g. on two unordered streams) race on it.  The first call on each device,
+ * made with that device current, looks up the array's device address; make
+ * that first call before any stream capture. */
+dw_status dw_apply_noalloc(const dw_field* U, const dw_field* in, dw_field* out, int dagger, dw_stream_t stream);
+
 /* ------------------------------------------------------------------ solvers */
 
 typedef struct {

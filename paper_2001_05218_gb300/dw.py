@@ -75,6 +75,7 @@ _SIGS = {
     "dw_apply": [_FP, _FP, _FP, _P],
     "dw_apply_dag": [_FP, _FP, _FP, _P],
     "dw_normal_apply": [_FP, _FP, _FP, _P],
+    "dw_apply_noalloc": [_FP, _FP, _FP, _I, _P],
     "dw_solver_params_default": [ctypes.POINTER(dw_solver_params)],
     "dw_cg_solve": [_FP, _FP, _FP, ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_solver_stats), _P],
     "dw_cg_solve_batched": [_I, ctypes.POINTER(_FP), ctypes.POINTER(_FP), ctypes.POINTER(_FP),
