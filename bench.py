@@ -234,6 +234,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--inner", default=None)
     ap.add_argument("--compress12", type=int, default=None)
+    ap.add_argument("--outer", default="df64", help="precision of the reliable updates: df64 or f64")
+    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold")
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -272,7 +274,9 @@ def main():
     Ug = dw.gauge(dims, kappa, U)
     bg = dw.spinor(dims, b)
     xg = dw.spinor(dims)
-    p_mix = dw.params(tol=1e-10, inner=inner, compress12=c12, maxiter=40000)
+    p_mix = dw.params(tol=1e-10, inner=inner, compress12=c12, maxiter=40000, outer=args.outer)
+    if args.delta is not None:
+        p_mix.delta = args.delta
     p_64 = dw.params(tol=1e-10, inner="f64", maxiter=40000)
     zero = torch.zeros(xg.nbytes, dtype=torch.uint8, device="cuda")
     l2_bytes = torch.cuda.get_device_properties(0).L2_cache_size
@@ -349,7 +353,7 @@ def main():
                 "bytes_per_launch": bpl, "ms_per_launch": pl_ms, "launches": e["launches"], "gflops": gfl}
 
     dom_name, dom = max(prof.items(), key=lambda kv: kv[1]["total_ms"])
-    inner_name = [k for k in prof if not k.startswith("hop f64")]
+    inner_name = [k for k in prof if not k.startswith("hop f64") and not k.startswith("hop df64")]
     hop_total_ms = sum(v["total_ms"] for v in prof.values())
 
     # FP64 CG on the same system, same GPU
@@ -363,7 +367,19 @@ def main():
         s64, st64 = dw.cg_solve(Ug, bg, xg, p_64)
         e1.record(stream)
         torch.cuda.synchronize()
-        fp64 = {"ms": e0.elapsed_time(e1), "iters": st64[0]["iters"], "true_rel_resid": st64[0]["true_rel_resid"]}
+        fp64 = {"ms": e0.elapsed_time(e1), "iters": st64[0]["iters"], "true_rel_resid": st64[0]["true_rel_resid"],
+                "arith": "IEEE FP64 throughout"}
+        # the same CG with every FP64 stencil in double-float arithmetic (FP64 storage size)
+        p_df = dw.params(tol=1e-10, inner="df64", maxiter=40000)
+        solve(p_df)
+        torch.cuda.synchronize()
+        reset_x()
+        e0.record(stream)
+        sdf, stdf = dw.cg_solve(Ug, bg, xg, p_df)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fp64["df64_cg"] = {"ms": e0.elapsed_time(e1), "iters": stdf[0]["iters"],
+                           "true_rel_resid": stdf[0]["true_rel_resid"]}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     e2e = None
@@ -408,10 +424,14 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": solve_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "%s-storage/fp32-arith inner, f64 reliable" % inner if inner != "f64" else "f64",
+        "vs_baseline": None,
+        "dtype": ("%s-storage/fp32-arith inner, %s reliable updates, f64 certification" % (inner, args.outer))
+        if inner not in ("f64", "df64") else inner,
         "data": "synthetic (seeded exp(i a H) links, Gaussian source)",
         "config": {"workload": wl, "lattice": list(dims), "kappa": kappa, "solver": "even-odd CGNR",
-                   "inner": inner, "compress12": c12, "tol": 1e-10, "global_batch": world, "parallelism": "replicas",
+                   "inner": inner, "compress12": c12, "outer": args.outer, "delta": p_mix.delta,
+                   "certification": "IEEE FP64",
+                   "tol": 1e-10, "global_batch": world, "parallelism": "replicas",
                    "l2": "flushed between steps" if flush else "inputs larger than L2 (%d MB working set)" %
                          (working_set >> 20)},
         "mixed_cg": {"ms": solve_ms, "iters": st0["iters"], "reliable_updates": st0["reliable_updates"],

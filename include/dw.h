@@ -65,7 +65,11 @@ typedef enum {
   DW_ERR_TIMEOUT = 8        /* device-side wall-time budget exhausted */
 } dw_status;
 
-typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3 } dw_prec;
+/* DW_DF64: each real stored as the unevaluated sum hi + lo of two FP32
+ * numbers (about 49 significant bits) with double-float arithmetic on the
+ * FP32 pipes; same size as FP64.  On GB300 the FP64 pipe runs at 1/61 of the
+ * FP32 rate, so FP64-class stencils are faster this way. */
+typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3, DW_DF64 = 4 } dw_prec;
 
 typedef enum {
   DW_GAUGE = 0,       /* links U_mu(x), all sites */
@@ -161,8 +165,9 @@ dw_status dw_apply_noalloc(const dw_field* U, const dw_field* in, dw_field* out,
 typedef struct {
   double tol;          /* stop when |b - D x| / |b| <= tol, recomputed in FP64 */
   int maxiter;         /* CG iteration limit */
-  dw_prec inner;       /* DW_F64: plain FP64 CG.  DW_F32/F16/BF16: mixed-precision
-                          CG with FP64 reliable updates */
+  dw_prec inner;       /* DW_F64: plain FP64 CG.  DW_DF64: plain CG in double-float.
+                          DW_F32/F16/BF16: mixed-precision CG with reliable updates
+                          in the `outer` precision */
   double delta;        /* reliable update when |r| < delta * |r at last update| */
   int eo;              /* 1: even-odd preconditioned (Schur system on even sites) */
   int compress12;      /* inner-precision links stored as 12 reals */
@@ -173,6 +178,10 @@ typedef struct {
   double timeout_s;    /* device-side time budget per solve (0 = none) */
   int verify_normal;   /* 1: also compute normal_rel_resid (two more FP64 operator
                           applications); 0: normal_rel_resid = -1 */
+  dw_prec outer;       /* precision of the accumulator x, the recomputed residual, the
+                          source preparation and reconstruction of a mixed solve:
+                          DW_F64 (IEEE) or DW_DF64.  The final residual that
+                          certifies every solve is IEEE FP64 either way. */
 } dw_solver_params;
 
 typedef struct {
@@ -188,7 +197,7 @@ typedef struct {
 
 /* Fill *p with defaults: tol 1e-10, maxiter 20000, inner DW_F32, delta 0.1,
  * eo 1, compress12 0, recompute_fwd 1, tile 0, check_every 0, timeout 0,
- * verify_normal 0.
+ * verify_normal 0, outer DW_F64.
  * The CG loop runs as one CUDA graph: a device-side while-loop over the
  * iteration, with the FP64 reliable update in a conditional node; the host
  * waits once per solve.  While dw_profile_start is active the loop is stepped

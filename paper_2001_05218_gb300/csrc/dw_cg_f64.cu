@@ -1,3 +1,3 @@
-// Instantiation of the CG solver for one (inner, accumulate, link-compression) choice.
+// Instantiation of the CG solver for one (inner, accumulate, link compression, high) choice.
 #include "dw_solver.cuh"
-template struct dw::CG<dw::P64, dw::P64, false>;
+template struct dw::CG<dw::P64, dw::P64, false, dw::P64>;

@@ -24,7 +24,93 @@
 
 namespace dw {
 
-enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3 };
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PDF = 4 };
+
+// ------------------------------------------------------------------ double-float
+// A real as the unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2),
+// about 49 significant bits, computed on the FP32 pipes.  The error-free
+// transforms are Knuth's TwoSum, Dekker's Fast2Sum and the FMA form of
+// TwoProduct; every step uses explicitly rounded intrinsics so the compiler
+// cannot contract or reorder them.
+struct DF {
+  float hi, lo;
+  DF() = default;
+  __host__ __device__ explicit DF(int v) : hi((float)v), lo(0.f) {}
+  __host__ __device__ explicit DF(float v) : hi(v), lo(0.f) {}
+  __device__ explicit DF(double d) {
+    hi = __double2float_rn(d);
+    lo = __double2float_rn(d - (double)hi);
+  }
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ explicit operator float() const { return hi + lo; }
+};
+
+__device__ __forceinline__ DF df_make(float h, float l) {
+  DF r;
+  r.hi = h;
+  r.lo = l;
+  return r;
+}
+// a + b exactly as s + e (Knuth)
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return df_make(s, e);
+}
+// a + b exactly as s + e when |a| >= |b| (Dekker)
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return df_make(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ DF operator-(DF a) { return df_make(-a.hi, -a.lo); }
+// hi parts added exactly, lo parts added in FP32, renormalised: the error is
+// below about 2u^2 (|a| + |b|), u = 2^-24, which is the scale the per-site
+// comparisons measure
+__device__ __forceinline__ DF operator+(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF operator-(DF a, DF b) { return a + (-b); }
+__device__ __forceinline__ DF operator*(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+// a*b + c (the float and double overloads stay visible next to this one)
+using ::fma;
+__device__ __forceinline__ DF fma(DF a, DF b, DF c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  const DF s = two_sum(p, c.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(c.lo, e)));
+}
+
+// Sum of n products x_i * y_i: exact high products chained with TwoSum, all
+// low-order terms collected in one FP32 accumulator, one renormalisation.
+template <int N>
+__device__ __forceinline__ DF df_dot(const DF (&x)[N], const DF (&y)[N]) {
+  float S = __fmul_rn(x[0].hi, y[0].hi);
+  float E = __fmaf_rn(x[0].hi, y[0].hi, -S);
+  E = __fmaf_rn(x[0].hi, y[0].lo, E);
+  E = __fmaf_rn(x[0].lo, y[0].hi, E);
+#pragma unroll
+  for (int i = 1; i < N; ++i) {
+    const float p = __fmul_rn(x[i].hi, y[i].hi);
+    E = __fadd_rn(E, __fmaf_rn(x[i].hi, y[i].hi, -p));
+    E = __fmaf_rn(x[i].hi, y[i].lo, E);
+    E = __fmaf_rn(x[i].lo, y[i].hi, E);
+    const DF t = two_sum(S, p);
+    S = t.hi;
+    E = __fadd_rn(E, t.lo);
+  }
+  return fast_two_sum(S, E);
+}
+
 
 // ------------------------------------------------------------------ complex
 template <typename R>
@@ -195,6 +281,28 @@ struct Spin<P16> : Spin16<P16> {};
 template <>
 struct Spin<PB16> : Spin16<PB16> {};
 
+// double-float: 12 planes of float4 (re.hi, re.lo, im.hi, im.lo)
+template <>
+struct Spin<PDF> {
+  using R = DF;
+  static constexpr int kBytes = 192;
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<DF> (&v)[12]) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      float4 t = __ldg(b + (size_t)k * vh + s);
+      v[k].re = df_make(t.x, t.y);
+      v[k].im = df_make(t.z, t.w);
+    }
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<DF> (&v)[12]) {
+    float4* b = reinterpret_cast<float4*>(base);
+#pragma unroll
+    for (int k = 0; k < 12; ++k) b[(size_t)k * vh + s] = make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
+  }
+  __device__ static __forceinline__ void roundtrip(Cx<DF> (&)[12]) {}
+};
+
 // ------------------------------------------------------------------ link storage
 template <typename R>
 __device__ __forceinline__ void rebuild_row2(Cx<R> (&u)[9]) {
@@ -270,6 +378,29 @@ struct Link<P32, true> {
   }
 };
 
+template <bool C12>
+struct Link<PDF, C12> {
+  using R = DF;
+  static constexpr int kBytes = C12 ? 96 : 144;
+  __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<DF> (&u)[9]) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+    constexpr int n = C12 ? 6 : 9;
+#pragma unroll
+    for (int k = 0; k < n; ++k) {
+      float4 t = __ldg(b + (size_t)k * vh + s);
+      u[k].re = df_make(t.x, t.y);
+      u[k].im = df_make(t.z, t.w);
+    }
+    if (C12) rebuild_row2(u);
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<DF> (&u)[9]) {
+    float4* b = reinterpret_cast<float4*>(base);
+    constexpr int n = C12 ? 6 : 9;
+#pragma unroll
+    for (int k = 0; k < n; ++k) b[(size_t)k * vh + s] = make_float4(u[k].re.hi, u[k].re.lo, u[k].im.hi, u[k].im.lo);
+  }
+};
+
 template <int P, bool C12>
 struct Link16 {
   using R = float;
@@ -339,11 +470,11 @@ struct Slot {
 
 enum SlotId {
   S_LLO = 0,   // inner-precision links
-  S_LHI,       // FP64 links
-  S_B,         // user source (FP64, full)
-  S_X,         // user solution (FP64, full) -- the FP64 accumulator
-  S_BH,        // prepared even source (FP64)
-  S_RT,        // FP64 residual / temporary (full: even = r64, odd = t64)
+  S_LHI,       // high-precision links (FP64 or double-float)
+  S_B,         // source b in the high precision (full)
+  S_X,         // high-precision accumulator x (full; the caller's field when high = FP64)
+  S_BH,        // prepared even source (high precision)
+  S_RT,        // high-precision residual / temporary (full: even = r, odd = t)
   S_XL,        // low-precision solution increment (accumulate precision)
   S_R,         // inner residual
   S_P,         // search direction
@@ -354,6 +485,9 @@ enum SlotId {
   S_AUX1,
   S_AUX2,
   S_AUX3,
+  S_XU,        // the caller's solution field (FP64)
+  S_BU,        // the caller's source field (FP64)
+  S_LF64,      // the caller's FP64 links (final certification)
   kNumSlots
 };
 

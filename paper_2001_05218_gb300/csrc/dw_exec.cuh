@@ -44,7 +44,9 @@ inline void count_launch() {
   Profiler& p = profiler();
   if (p.on) p.launches += 1;
 }
-inline const char* prec_name(int p) { return p == P64 ? "f64" : p == P32 ? "f32" : p == P16 ? "f16" : "bf16"; }
+inline const char* prec_name(int p) {
+  return p == P64 ? "f64" : p == P32 ? "f32" : p == P16 ? "f16" : p == PB16 ? "bf16" : "df64";
+}
 
 struct Exec {
   Plan P;

@@ -34,6 +34,7 @@ int spin_bytes(int prec) {
     case DW_F32: return Spin<P32>::kBytes;
     case DW_F16: return Spin<P16>::kBytes;
     case DW_BF16: return Spin<PB16>::kBytes;
+    case DW_DF64: return Spin<PDF>::kBytes;
   }
   return 0;
 }
@@ -44,6 +45,7 @@ int link_bytes(int prec, int c12) {
     case DW_F32: return c12 ? Link<P32, true>::kBytes : Link<P32, false>::kBytes;
     case DW_F16: return c12 ? Link<P16, true>::kBytes : Link<P16, false>::kBytes;
     case DW_BF16: return c12 ? Link<PB16, true>::kBytes : Link<PB16, false>::kBytes;
+    case DW_DF64: return c12 ? Link<PDF, true>::kBytes : Link<PDF, false>::kBytes;
   }
   return 0;
 }
@@ -256,6 +258,7 @@ static Dims4 dims4(const dw_lattice& l) {
     case DW_F32: { constexpr int PP = P32; BODY; } break;  \
     case DW_F16: { constexpr int PP = P16; BODY; } break;  \
     case DW_BF16: { constexpr int PP = PB16; BODY; } break; \
+    case DW_DF64: { constexpr int PP = PDF; BODY; } break; \
   }
 
 dw_status pack_spinor_from_canonical(dw_field* f, const double* dev, cudaStream_t st) {
@@ -404,7 +407,7 @@ dw_status dw_field_bytes(const dw_lattice* lat, dw_kind kind, dw_prec prec, int 
                          size_t* bytes) {
   DW_TRY(check_lattice(lat));
   DW_CHECK(bytes != nullptr, DW_ERR_ARG, "bytes is NULL");
-  DW_CHECK(prec >= DW_F64 && prec <= DW_BF16, DW_ERR_PRECISION, "unknown precision %d", (int)prec);
+  DW_CHECK(prec >= DW_F64 && prec <= DW_DF64, DW_ERR_PRECISION, "unknown precision %d", (int)prec);
   DW_CHECK(kind >= DW_GAUGE && kind <= DW_SPINOR_ODD, DW_ERR_ARG, "unknown field kind %d", (int)kind);
   const long long vh = vh_of(*lat);
   if (kind == DW_GAUGE) {

@@ -103,6 +103,90 @@ __device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6]
     }
 }
 
+// Double-float version: each real output is one 6-term dot product.
+template <bool ADJ>
+__device__ __forceinline__ void su3_mul(const Cx<DF> (&u)[9], const Cx<DF> (&h)[6], Cx<DF> (&g)[6]) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      DF xr[6], yr[6], xi[6], yi[6];
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const Cx<DF> m = ADJ ? u[b * 3 + a] : u[a * 3 + b];
+        const Cx<DF> v = h[3 * k + b];
+        // re = m.re v.re -/+ m.im v.im ; im = m.re v.im +/- m.im v.re  (lower sign: adjoint)
+        xr[2 * b] = m.re;
+        yr[2 * b] = v.re;
+        xr[2 * b + 1] = ADJ ? m.im : -m.im;
+        yr[2 * b + 1] = v.im;
+        xi[2 * b] = m.re;
+        yi[2 * b] = v.im;
+        xi[2 * b + 1] = ADJ ? -m.im : m.im;
+        yi[2 * b + 1] = v.re;
+      }
+      g[3 * k + a].re = df_dot(xr, yr);
+      g[3 * k + a].im = df_dot(xi, yi);
+    }
+}
+
+// Runtime-direction form of the spin projection and reconstruction, used by
+// the double-float stencil whose unrolled body would not fit the instruction
+// cache.  For (1 + s gamma_mu):  h0 = p0 + c0 q0,  h1 = p1 + c1 q1 with
+// (q0, q1) = (p3, p2) for mu = x, y and (p2, p3) for mu = z, t; the lower spins
+// are d2 (g1 or g0) and d3 (g0 or g1) with the same pairing.  Every factor is
+// +-1 or +-i:
+//   mu = x: c0 = c1 = -s i;   d2 = d3 = s i
+//   mu = y: c0 = -s, c1 = s;  d2 = s, d3 = -s
+//   mu = z: c0 = -s i, c1 = s i; d2 = s i, d3 = -s i
+//   mu = t: c0 = c1 = s;      d2 = d3 = s
+struct UnitFactor {
+  bool imag;   // multiply by i
+  bool neg;    // then by -1
+};
+template <typename R>
+__device__ __forceinline__ Cx<R> mul_unit(Cx<R> q, UnitFactor f) {
+  Cx<R> r = f.imag ? cx(-q.im, q.re) : q;
+  return f.neg ? cx(-r.re, -r.im) : r;
+}
+struct DirSpin {
+  bool swap;  // pair spin 0 with spin 3 (x, y)
+  UnitFactor c0, c1, d2, d3;
+};
+__device__ __forceinline__ DirSpin dir_spin(int mu, int s) {
+  DirSpin d;
+  const bool neg_s = s < 0;
+  d.swap = mu <= 1;
+  const bool im = (mu == 0 || mu == 2);
+  d.c0 = UnitFactor{im, mu == 3 ? neg_s : !neg_s};
+  d.c1 = UnitFactor{im, mu == 0 ? !neg_s : neg_s};
+  d.d2 = UnitFactor{im, neg_s};
+  d.d3 = UnitFactor{im, (mu == 1 || mu == 2) ? !neg_s : neg_s};
+  return d;
+}
+template <typename R>
+__device__ __forceinline__ void project_rt(const DirSpin& d, const Cx<R> (&p)[12], Cx<R> (&h)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const Cx<R> q0 = d.swap ? p[9 + c] : p[6 + c];
+    const Cx<R> q1 = d.swap ? p[6 + c] : p[9 + c];
+    h[c] = p[c] + mul_unit(q0, d.c0);
+    h[3 + c] = p[3 + c] + mul_unit(q1, d.c1);
+  }
+}
+template <typename R>
+__device__ __forceinline__ void accumulate_rt(const DirSpin& d, Cx<R> (&acc)[12], const Cx<R> (&g)[6]) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = acc[c] + g[c];
+    acc[3 + c] = acc[3 + c] + g[3 + c];
+    const Cx<R> g2 = d.swap ? g[3 + c] : g[c];
+    const Cx<R> g3 = d.swap ? g[c] : g[3 + c];
+    acc[6 + c] = acc[6 + c] + mul_unit(g2, d.d2);
+    acc[9 + c] = acc[9 + c] + mul_unit(g3, d.d3);
+  }
+}
+
 // Site coordinates of even-odd index s on parity par.
 struct Coord {
   int xh, x, y, z, t, row;  // row = s - xh (start of the x-row in eo indexing)
@@ -156,6 +240,15 @@ __device__ __forceinline__ int neighbour(const SysDesc& S, const Coord& c, int s
   }
 }
 
+__device__ __forceinline__ int neighbour_rt(const SysDesc& S, const Coord& c, int s, int mu, int dir, float* eta) {
+  switch (mu) {
+    case 0: return dir > 0 ? neighbour<0, +1>(S, c, s, eta) : neighbour<0, -1>(S, c, s, eta);
+    case 1: return dir > 0 ? neighbour<1, +1>(S, c, s, eta) : neighbour<1, -1>(S, c, s, eta);
+    case 2: return dir > 0 ? neighbour<2, +1>(S, c, s, eta) : neighbour<2, -1>(S, c, s, eta);
+    default: return dir > 0 ? neighbour<3, +1>(S, c, s, eta) : neighbour<3, -1>(S, c, s, eta);
+  }
+}
+
 __device__ __forceinline__ const char* slot_ptr(const SysDesc& S, int slot, int r, int par) {
   const Slot& f = S.f[slot];
   return f.p + r * f.rhs_stride + par * f.par_stride;
@@ -186,19 +279,21 @@ struct InOne {
   }
 };
 
-// Neighbour spinor x + xl: the FP64 accumulator plus the low-precision increment.
-template <int SPL>
+// Neighbour spinor x + xl: the high-precision accumulator plus the
+// low-precision increment.
+template <int SPH, int SPL>
 struct InSum {
   int slot_x, slot_xl;
-  __host__ double io_bytes() const { return Spin<P64>::kBytes + Spin<SPL>::kBytes; }
+  __host__ double io_bytes() const { return Spin<SPH>::kBytes + Spin<SPL>::kBytes; }
   template <typename R>
   __device__ __forceinline__ void load(const SysDesc& S, int par, int r, int s, Cx<R> (&v)[12]) const {
-    Cx<double> a[12];
+    using RH = typename Spin<SPH>::R;
+    Cx<RH> a[12];
     Cx<typename Spin<SPL>::R> b[12];
-    Spin<P64>::load(slot_ptr(S, slot_x, r, par), S.vh, s, a);
+    Spin<SPH>::load(slot_ptr(S, slot_x, r, par), S.vh, s, a);
     Spin<SPL>::load(slot_ptr(S, slot_xl, r, par), S.vh, s, b);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = cx((R)(a[k].re + (double)b[k].re), (R)(a[k].im + (double)b[k].im));
+    for (int k = 0; k < 12; ++k) v[k] = cx((R)(a[k].re + (RH)b[k].re), (R)(a[k].im + (RH)b[k].im));
   }
 };
 
@@ -236,7 +331,7 @@ struct EpiXpay {
     Spin<SPX>::load(slot_ptr(S, slot_x, r, par), S.vh, s, xv);
     const R c = (R)coef_of<COEF>(S.kappa);
     Cx<RO> o[12];
-    R n = 0;
+    R n = (R)0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       R re = fma(c, acc[k].re, (R)xv[k].re), im = fma(c, acc[k].im, (R)xv[k].im);
@@ -248,37 +343,39 @@ struct EpiXpay {
   }
 };
 
-// Reliable update on the even-odd system (FP64), at even site s:
-//   x <- x + xl;  xl <- 0;  r64 = bh - x + kappa^2 * acc  (acc = H_eo t64);
-//   r_low <- r64;  reduction |r64|^2.
-template <int SPL, int SPA>
+// Reliable update on the even-odd system, in the high precision SPH, at even site s:
+//   x <- x + xl;  xl <- 0;  r_hi = bh - x + kappa^2 * acc  (acc = H_eo t_hi);
+//   r_low <- r_hi;  reduction |r_hi|^2.
+template <int SPL, int SPA, int SPH>
 struct EpiReliableEO {
   static constexpr bool kReduce = true;
   int gate;
   __host__ double io_bytes() const {
-    return 4.0 * Spin<P64>::kBytes + 2.0 * Spin<SPA>::kBytes + Spin<SPL>::kBytes;
+    return 4.0 * Spin<SPH>::kBytes + 2.0 * Spin<SPA>::kBytes + Spin<SPL>::kBytes;
   }
-  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<double> (&acc)[12],
+  template <typename RH>
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<RH> (&acc)[12],
                                         double& nrm) const {
-    Cx<double> x[12], bh[12], rv[12];
-    Cx<typename Spin<SPA>::R> xl[12];
-    Spin<P64>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
+    using RA = typename Spin<SPA>::R;
+    Cx<RH> x[12], bh[12], rv[12];
+    Cx<RA> xl[12];
+    Spin<SPH>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
     Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
-    Spin<P64>::load(slot_ptr(S, S_BH, r, par), S.vh, s, bh);
-    const double k2 = S.kappa * S.kappa;
-    double n = 0;
-    Cx<typename Spin<SPA>::R> zero[12];
+    Spin<SPH>::load(slot_ptr(S, S_BH, r, par), S.vh, s, bh);
+    const RH k2 = (RH)(S.kappa * S.kappa);
+    RH n = (RH)0;
+    Cx<RA> zero[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      x[k] = cx(x[k].re + (double)xl[k].re, x[k].im + (double)xl[k].im);
+      x[k] = cx(x[k].re + (RH)xl[k].re, x[k].im + (RH)xl[k].im);
       rv[k] = cx(fma(k2, acc[k].re, bh[k].re - x[k].re), fma(k2, acc[k].im, bh[k].im - x[k].im));
       n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
-      zero[k] = cx((typename Spin<SPA>::R)0, (typename Spin<SPA>::R)0);
+      zero[k] = cx((RA)0, (RA)0);
     }
-    nrm = n;
-    Spin<P64>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
+    nrm = (double)n;
+    Spin<SPH>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
     Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, zero);
-    Spin<P64>::store(slot_wptr(S, S_RT, r, par), S.vh, s, rv);
+    Spin<SPH>::store(slot_wptr(S, S_RT, r, par), S.vh, s, rv);
     Cx<typename Spin<SPL>::R> lo[12];
     convert12(rv, lo);
     Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, lo);
@@ -286,9 +383,9 @@ struct EpiReliableEO {
 };
 
 // Full-lattice residual rt = b - (x - kappa*acc) on the output parity (with
-// acc = H x this is b - D x; with acc = Hdag x it is b - D^dag x),
-// optionally also r_low <- rt.  Reduction |rt|^2.
-template <int SPL, bool STORE_LOW>
+// acc = H x this is b - D x; with acc = Hdag x it is b - D^dag x), in the
+// precision SPH of x, b and rt, optionally also r_low <- rt.  Reduction |rt|^2.
+template <int SPL, bool STORE_LOW, int SPH>
 struct EpiResidFull {
   static constexpr bool kReduce = true;
   int gate;
@@ -296,21 +393,23 @@ struct EpiResidFull {
   int slot_x;
   int slot_b;
   __host__ double io_bytes() const {
-    return 2.0 * Spin<P64>::kBytes + (slot_rt >= 0 ? Spin<P64>::kBytes : 0) + (STORE_LOW ? Spin<SPL>::kBytes : 0);
+    return 2.0 * Spin<SPH>::kBytes + (slot_rt >= 0 ? Spin<SPH>::kBytes : 0) + (STORE_LOW ? Spin<SPL>::kBytes : 0);
   }
-  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<double> (&acc)[12],
+  template <typename RH>
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<RH> (&acc)[12],
                                         double& nrm) const {
-    Cx<double> x[12], b[12], rv[12];
-    Spin<P64>::load(slot_ptr(S, slot_x, r, par), S.vh, s, x);
-    Spin<P64>::load(slot_ptr(S, slot_b, r, par), S.vh, s, b);
-    double n = 0;
+    Cx<RH> x[12], b[12], rv[12];
+    Spin<SPH>::load(slot_ptr(S, slot_x, r, par), S.vh, s, x);
+    Spin<SPH>::load(slot_ptr(S, slot_b, r, par), S.vh, s, b);
+    const RH kap = (RH)S.kappa;
+    RH n = (RH)0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      rv[k] = cx(fma(S.kappa, acc[k].re, b[k].re - x[k].re), fma(S.kappa, acc[k].im, b[k].im - x[k].im));
+      rv[k] = cx(fma(kap, acc[k].re, b[k].re - x[k].re), fma(kap, acc[k].im, b[k].im - x[k].im));
       n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
     }
-    nrm = n;
-    if (slot_rt >= 0) Spin<P64>::store(slot_wptr(S, slot_rt, r, par), S.vh, s, rv);
+    nrm = (double)n;
+    if (slot_rt >= 0) Spin<SPH>::store(slot_wptr(S, slot_rt, r, par), S.vh, s, rv);
     if (STORE_LOW) {
       Cx<typename Spin<SPL>::R> lo[12];
       convert12(rv, lo);
@@ -403,10 +502,40 @@ __global__ void __launch_bounds__(256) k_hop(const __grid_constant__ Batch B, in
     su3_mul<true>(u, h, g);                                                     \
     accumulate<MU, SB>(acc, g);                                                 \
   }
-    DW_HOP_DIR(0)
-    DW_HOP_DIR(1)
-    DW_HOP_DIR(2)
-    DW_HOP_DIR(3)
+    if constexpr (SPA == PDF) {
+      // compact loop: one copy of the double-float mat-vec per (U, U^dag)
+#pragma unroll 1
+      for (int mu = 0; mu < 4; ++mu) {
+        float eta;
+        Cx<R> p[12], h[6], g[6], u[9];
+        const DirSpin df = dir_spin(mu, SF), db = dir_spin(mu, SB);
+        const int nf = neighbour_rt(S, c, s, mu, +1, &eta);
+        in.load(S, pin, r, nf, p);
+        project_rt(df, p, h);
+        Link<LP, C12>::load(ulink_own + mu * mu_stride, S.vh, s, u);
+        if (eta < 0.f) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im);
+        }
+        su3_mul<false>(u, h, g);
+        accumulate_rt(df, acc, g);
+        const int nb = neighbour_rt(S, c, s, mu, -1, &eta);
+        in.load(S, pin, r, nb, p);
+        project_rt(db, p, h);
+        Link<LP, C12>::load(ulink_nb + mu * mu_stride, S.vh, nb, u);
+        if (eta < 0.f) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im);
+        }
+        su3_mul<true>(u, h, g);
+        accumulate_rt(db, acc, g);
+      }
+    } else {
+      DW_HOP_DIR(0)
+      DW_HOP_DIR(1)
+      DW_HOP_DIR(2)
+      DW_HOP_DIR(3)
+    }
 #undef DW_HOP_DIR
     epi.write(S, par, r, s, acc, nrm);
   }
@@ -431,7 +560,7 @@ __global__ void __launch_bounds__(256) k_update_xr(const __grid_constant__ Batch
     Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
     const RL a = (RL)alpha;
     const RA aa = (RA)alpha;
-    RL n = 0;
+    RL n = (RL)0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       xl[k] = cx(fma(aa, (RA)p[k].re, xl[k].re), fma(aa, (RA)p[k].im, xl[k].im));
@@ -467,16 +596,18 @@ __global__ void __launch_bounds__(256) k_update_p(const __grid_constant__ Batch 
 }
 
 // First residual for a zero initial guess: r_low = src, reduction |src|^2 -> FIN_RESID0
-template <int SPL>
+template <int SPL, int SPH>
 __global__ void __launch_bounds__(256) k_init_r(const __grid_constant__ Batch B, int par_mode, int slot_src, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_XZERO)
   double nrm = 0.0;
   if (valid) {
-    Cx<double> v[12];
+    using RH = typename Spin<SPH>::R;
+    Cx<RH> v[12];
     Cx<typename Spin<SPL>::R> lo[12];
-    Spin<P64>::load(slot_ptr(S, slot_src, r, par), S.vh, s, v);
+    Spin<SPH>::load(slot_ptr(S, slot_src, r, par), S.vh, s, v);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) nrm = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, nrm));
+    for (int k = 0; k < 12; ++k)
+      nrm = fma((double)v[k].re, (double)v[k].re, fma((double)v[k].im, (double)v[k].im, nrm));
     convert12(v, lo);
     Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, lo);
   }
@@ -484,21 +615,22 @@ __global__ void __launch_bounds__(256) k_init_r(const __grid_constant__ Batch B,
 }
 
 // x += xl; xl = 0   (full-lattice reliable update, both parities)
-template <int SPA>
+template <int SPA, int SPH>
 __global__ void __launch_bounds__(256) k_fold_x(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_REL)
   if (valid) {
     using RA = typename Spin<SPA>::R;
-    Cx<double> x[12];
+    using RH = typename Spin<SPH>::R;
+    Cx<RH> x[12];
     Cx<RA> xl[12];
-    Spin<P64>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
+    Spin<SPH>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
     Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      x[k] = cx(x[k].re + (double)xl[k].re, x[k].im + (double)xl[k].im);
+      x[k] = cx(x[k].re + (RH)xl[k].re, x[k].im + (RH)xl[k].im);
       xl[k] = cx((RA)0, (RA)0);
     }
-    Spin<P64>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
+    Spin<SPH>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
     Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, xl);
   }
 }

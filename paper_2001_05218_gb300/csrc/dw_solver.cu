@@ -3,31 +3,49 @@
 
 namespace dw {
 
-extern template struct CG<P64, P64, false>;
-extern template struct CG<P32, P32, false>;
-extern template struct CG<P32, P32, true>;
-extern template struct CG<P16, P32, false>;
-extern template struct CG<P16, P32, true>;
-extern template struct CG<PB16, P32, false>;
-extern template struct CG<PB16, P32, true>;
+#define DW_CG_EXTERN(L, A, C, H) extern template struct CG<L, A, C, H>;
+DW_CG_EXTERN(P64, P64, false, P64)
+DW_CG_EXTERN(PDF, PDF, false, PDF)
+DW_CG_EXTERN(P32, P32, false, P64)
+DW_CG_EXTERN(P32, P32, true, P64)
+DW_CG_EXTERN(P16, P32, false, P64)
+DW_CG_EXTERN(P16, P32, true, P64)
+DW_CG_EXTERN(PB16, P32, false, P64)
+DW_CG_EXTERN(PB16, P32, true, P64)
+DW_CG_EXTERN(P32, P32, false, PDF)
+DW_CG_EXTERN(P32, P32, true, PDF)
+DW_CG_EXTERN(P16, P32, false, PDF)
+DW_CG_EXTERN(P16, P32, true, PDF)
+DW_CG_EXTERN(PB16, P32, false, PDF)
+DW_CG_EXTERN(PB16, P32, true, PDF)
+#undef DW_CG_EXTERN
 
-static dw_status dispatch(const SolveArgs& a) {
+template <int H>
+static dw_status dispatch_inner(const SolveArgs& a) {
   const bool c = a.p.compress12 != 0;
   switch (a.p.inner) {
-    case DW_F64: return CG<P64, P64, false>::run(a);
-    case DW_F32: return c ? CG<P32, P32, true>::run(a) : CG<P32, P32, false>::run(a);
-    case DW_F16: return c ? CG<P16, P32, true>::run(a) : CG<P16, P32, false>::run(a);
-    case DW_BF16: return c ? CG<PB16, P32, true>::run(a) : CG<PB16, P32, false>::run(a);
+    case DW_F32: return c ? CG<P32, P32, true, H>::run(a) : CG<P32, P32, false, H>::run(a);
+    case DW_F16: return c ? CG<P16, P32, true, H>::run(a) : CG<P16, P32, false, H>::run(a);
+    case DW_BF16: return c ? CG<PB16, P32, true, H>::run(a) : CG<PB16, P32, false, H>::run(a);
+    default: break;
   }
   return set_error(DW_ERR_PRECISION, "unknown inner precision %d", (int)a.p.inner);
+}
+
+static dw_status dispatch(const SolveArgs& a) {
+  if (a.p.inner == DW_F64) return CG<P64, P64, false, P64>::run(a);
+  if (a.p.inner == DW_DF64) return CG<PDF, PDF, false, PDF>::run(a);
+  return a.p.outer == DW_DF64 ? dispatch_inner<PDF>(a) : dispatch_inner<P64>(a);
 }
 
 static dw_status check_params(const dw_solver_params* p) {
   DW_CHECK(p != nullptr, DW_ERR_ARG, "params is NULL");
   DW_CHECK(p->tol > 0 && p->tol < 1, DW_ERR_ARG, "tol %g must lie in (0, 1)", p->tol);
   DW_CHECK(p->maxiter > 0, DW_ERR_ARG, "maxiter must be positive");
-  DW_CHECK(p->inner >= DW_F64 && p->inner <= DW_BF16, DW_ERR_PRECISION, "unknown inner precision");
-  DW_CHECK(p->inner == DW_F64 || (p->delta > 0 && p->delta < 1), DW_ERR_ARG, "delta %g must lie in (0, 1)",
+  DW_CHECK(p->inner >= DW_F64 && p->inner <= DW_DF64, DW_ERR_PRECISION, "unknown inner precision");
+  DW_CHECK(p->outer == DW_F64 || p->outer == DW_DF64, DW_ERR_PRECISION, "outer precision must be DW_F64 or DW_DF64");
+  DW_CHECK(p->inner == DW_F64 || p->inner == DW_DF64 || (p->delta > 0 && p->delta < 1), DW_ERR_ARG,
+           "delta %g must lie in (0, 1)",
            p->delta);
   DW_CHECK(p->tile == 0 || (p->tile >= 32 && p->tile <= 256 && p->tile % 32 == 0), DW_ERR_ARG,
            "tile %d must be 0 or a multiple of 32 in [32, 256]", p->tile);
@@ -91,6 +109,7 @@ dw_status dw_solver_params_default(dw_solver_params* p) {
   p->check_every = 0;
   p->timeout_s = 0;
   p->verify_normal = 0;
+  p->outer = DW_F64;
   return DW_OK;
 }
 

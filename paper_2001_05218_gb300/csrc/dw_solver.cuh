@@ -1,5 +1,5 @@
-// dw_solver.cuh -- conjugate gradient on the GPU, mixed precision with FP64
-// reliable updates.
+// dw_solver.cuh -- conjugate gradient on the GPU, mixed precision with
+// high-precision reliable updates.
 //
 // The paper (Sec. 2, Sec. 3.3) runs most CG iterations in a low-precision
 // type and corrects "for a possible bias" in high precision now and then.
@@ -9,6 +9,13 @@
 // low-precision increment and the residual is recomputed in FP64 from the
 // definition (b - A x).  With inner = FP64 the same code is plain FP64 CG
 // whose residual is only recomputed at the convergence check.
+//
+// The high precision H of the accumulator, the recomputed residual, the
+// source preparation and the reconstruction is either IEEE FP64 or
+// double-float (two FP32 numbers, ~49 bits, computed on the FP32 pipes: on
+// GB300 the FP64 pipe runs at 1/61 of the FP32 rate).  The final residual
+// that certifies the solve is always recomputed in IEEE FP64 from the
+// caller's x, b and links.
 //
 // Three systems share the machinery (A = operator, r = b - A x tracked):
 //   MODE_EO     CGNR on the even-site Schur complement Dhat = 1 - k^2 H_eo H_oe:
@@ -49,7 +56,7 @@ static __global__ void k_set_deadline(ColState* cols, int n, unsigned long long 
   if (i < n && budget_ns) cols[i].deadline_ns = globaltimer_ns() + budget_ns;
 }
 
-template <int L, int A, bool C12>
+template <int L, int A, bool C12, int H>
 struct CG {
   static constexpr int kLinkHi = S_LHI;
   static constexpr int kLinkLo = S_LLO;
@@ -57,20 +64,20 @@ struct CG {
   // reliable update (gated by do_rel) and its finalizer
   static void reliable(const Exec& E, int mode) {
     if (mode == MODE_EO) {
-      hop<P64, P64, false, false>(E, 1, kLinkHi, InSum<A>{S_X, S_XL}, EpiOut<P64, C_ONE>{S_RT, G_REL});
-      hop<P64, P64, false, false>(E, 0, kLinkHi, InOne<P64>{S_RT}, EpiReliableEO<L, A>{G_REL}, FIN_RELIABLE);
+      hop<H, H, false, false>(E, 1, kLinkHi, InSum<H, A>{S_X, S_XL}, EpiOut<H, C_ONE>{S_RT, G_REL});
+      hop<H, H, false, false>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiReliableEO<L, A, H>{G_REL}, FIN_RELIABLE);
     } else if (mode == MODE_FULL) {
       count_launch();
-      k_fold_x<A><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
-      hop<P64, P64, false, false>(E, 2, kLinkHi, InOne<P64>{S_X}, EpiResidFull<L, true>{G_REL, S_RT, S_X, S_B},
-                                  FIN_RELIABLE);
+      k_fold_x<A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
+      hop<H, H, false, false>(E, 2, kLinkHi, InOne<H>{S_X}, EpiResidFull<L, true, H>{G_REL, S_RT, S_X, S_B},
+                              FIN_RELIABLE);
     } else {
       count_launch();
-      k_fold_x<A><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
-      // t64 = D x ; r64 = b - D^dag t64
-      hop<P64, P64, false, false>(E, 2, kLinkHi, InOne<P64>{S_X}, EpiXpay<P64, P64, C_MK, false>{S_AUX0, S_X, G_REL});
-      hop<P64, P64, false, true>(E, 2, kLinkHi, InOne<P64>{S_AUX0},
-                                 EpiResidFull<L, true>{G_REL, S_RT, S_AUX0, S_B}, FIN_RELIABLE);
+      k_fold_x<A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
+      // t = D x ; r = b - D^dag t
+      hop<H, H, false, false>(E, 2, kLinkHi, InOne<H>{S_X}, EpiXpay<H, H, C_MK, false>{S_AUX0, S_X, G_REL});
+      hop<H, H, false, true>(E, 2, kLinkHi, InOne<H>{S_AUX0}, EpiResidFull<L, true, H>{G_REL, S_RT, S_AUX0, S_B},
+                             FIN_RELIABLE);
     }
   }
 
@@ -128,8 +135,8 @@ struct CaptureStreams {
 // reliable update in an if-node }.  Both conditions are set on the device,
 // the loop is capped at maxiter + 2 passes, and every column also leaves the
 // loop through its own maxiter / timeout / breakdown checks.
-template <int L, int A, bool C12>
-dw_status CG<L, A, C12>::run_graph(const Exec& E0, int mode, int* body_kernels, int* rel_kernels) {
+template <int L, int A, bool C12, int H>
+dw_status CG<L, A, C12, H>::run_graph(const Exec& E0, int mode, int* body_kernels, int* rel_kernels) {
   static thread_local CaptureStreams cs;
   const int pm = mode == MODE_EO ? 0 : 2;
   cudaGraph_t g = nullptr;
@@ -205,8 +212,8 @@ dw_status CG<L, A, C12>::run_graph(const Exec& E0, int mode, int* body_kernels, 
 // Host-stepped loop: identical kernels, the host reads the device counters
 // after every update so that no launch is made without work; used while the
 // launch profiler is active.
-template <int L, int A, bool C12>
-dw_status CG<L, A, C12>::run_stepped(const Exec& E, int mode, int maxiter) {
+template <int L, int A, bool C12, int H>
+dw_status CG<L, A, C12, H>::run_stepped(const Exec& E, int mode, int maxiter) {
   static Flags* hf = nullptr;
   if (!hf) DW_CUDA(cudaMallocHost((void**)&hf, sizeof(Flags)));
   const int pm = mode == MODE_EO ? 0 : 2;
@@ -235,8 +242,8 @@ struct Arena {
   size_t bytes = 0;
 };
 
-template <int L, int A, bool C12>
-dw_status CG<L, A, C12>::run(const SolveArgs& a) {
+template <int L, int A, bool C12, int H>
+dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
   const int n = a.n;
   const int mode = a.mode;
   const int nrhs = a.b[0]->nrhs;
@@ -256,14 +263,20 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
   struct Piece { int slot, prec, npar; };
   std::vector<Piece> pieces;
   if (eo) {
-    pieces = {{S_BH, DW_F64, 1}, {S_RT, DW_F64, 2}, {S_XL, A, 1}, {S_R, L, 1},
-              {S_P, L, 1},       {S_Z, L, 1},       {S_W, L, 1},  {S_T, L, 1}};
+    pieces = {{S_BH, H, 1}, {S_RT, H, 2}, {S_XL, A, 1}, {S_R, L, 1},
+              {S_P, L, 1},  {S_Z, L, 1},  {S_W, L, 1},  {S_T, L, 1}};
   } else if (mode == MODE_FULL) {
-    pieces = {{S_RT, DW_F64, 2}, {S_XL, A, 2}, {S_R, L, 2}, {S_P, L, 2}, {S_Z, L, 2}, {S_W, L, 2}};
+    pieces = {{S_RT, H, 2}, {S_XL, A, 2}, {S_R, L, 2}, {S_P, L, 2}, {S_Z, L, 2}, {S_W, L, 2}};
   } else {
-    pieces = {{S_RT, DW_F64, 2}, {S_AUX0, DW_F64, 2}, {S_XL, A, 2}, {S_R, L, 2},
-              {S_P, L, 2},       {S_W, L, 2},         {S_T, L, 2}};
+    pieces = {{S_RT, H, 2}, {S_AUX0, H, 2}, {S_XL, A, 2}, {S_R, L, 2},
+              {S_P, L, 2},  {S_W, L, 2},    {S_T, L, 2}};
   }
+  if (H != P64) {  // high-precision copies of the caller's x and b
+    pieces.push_back({S_X, H, 2});
+    pieces.push_back({S_B, H, 2});
+  }
+  // FP64 full temporary for the certification (the FP64 arena piece doubles as it when H = FP64)
+  if ((a.p.verify_normal && H != P64) || (mode == MODE_NORMAL && H != P64)) pieces.push_back({S_AUX1, DW_F64, 2});
   size_t total = 0;
   std::vector<std::vector<size_t>> poff(n);
   for (int i = 0; i < n; ++i) {
@@ -294,9 +307,15 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
     status = derived_links(a.U[i], L, C12 ? 1 : 0, st, &lo);
     if (status != DW_OK) break;
     S.f[S_LLO] = gauge_slot(lo, lats[i], L, C12 ? 1 : 0);
-    S.f[S_LHI] = gauge_slot(a.U[i]->ptr, lats[i], DW_F64, 0);
-    S.f[S_B] = spinor_slot(a.b[i]);
-    S.f[S_X] = spinor_slot(a.x[i]);
+    const char* hi = nullptr;
+    status = derived_links(a.U[i], H, 0, st, &hi);
+    if (status != DW_OK) break;
+    S.f[S_LHI] = gauge_slot(hi, lats[i], H, 0);
+    S.f[S_LF64] = gauge_slot(a.U[i]->ptr, lats[i], DW_F64, 0);
+    S.f[S_BU] = spinor_slot(a.b[i]);
+    S.f[S_XU] = spinor_slot(a.x[i]);
+    S.f[S_B] = S.f[S_BU];
+    S.f[S_X] = S.f[S_XU];
     for (size_t k = 0; k < pieces.size(); ++k)
       S.f[pieces[k].slot] = arena_slot(arena + poff[i][k], lats[i], pieces[k].prec, nrhs, pieces[k].npar);
     if (mode == MODE_NORMAL) S.f[S_Z] = S.f[S_R];
@@ -311,7 +330,7 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
   for (auto& c : hc) {
     memset(&c, 0, sizeof c);
     c.tol2 = a.p.tol * a.p.tol;
-    c.delta2 = L == P64 ? 0.0 : a.p.delta * a.p.delta;
+    c.delta2 = (L == P64 || L == PDF) ? 0.0 : a.p.delta * a.p.delta;
     c.maxiter = a.p.maxiter;
     c.active = 1;
     c.do_rel = 1;  // the first FP64 residual is a "reliable update" unless x0 = 0
@@ -336,8 +355,14 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
   }
 
   // ---- set-up
-  norm<P64>(E, 2, S_B, FIN_BNORM);
-  norm<P64>(E, eo ? 0 : 2, S_X, FIN_XNORM);
+  norm<P64>(E, 2, S_BU, FIN_BNORM);
+  norm<P64>(E, eo ? 0 : 2, S_XU, FIN_XNORM);
+  if (H != P64) {
+    count_launch();
+    k_convert<H, P64><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_B, S_BU, E.ra(FIN_STORE0));
+    count_launch();
+    k_convert<H, P64><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_X, S_XU, E.ra(FIN_STORE0));
+  }
   for (int i = 0; i < n; ++i) {
     const SysDesc& S = E.P.B.sd[i];
     for (auto pc : {S_XL, S_P}) {
@@ -347,17 +372,22 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
   }
   if (eo) {
     // bh = b_e + kappa H_eo b_o
-    hop<P64, P64, false, false>(E, 0, kLinkHi, InOne<P64>{S_B}, EpiXpay<P64, P64, C_PK, false>{S_BH, S_B, G_ALL});
+    hop<H, H, false, false>(E, 0, kLinkHi, InOne<H>{S_B}, EpiXpay<H, H, C_PK, false>{S_BH, S_B, G_ALL});
   }
-  if (mode != MODE_NORMAL) {
-    // zero guess: r = source (bh or b); otherwise r = source - A x in FP64
-    count_launch();
-    k_init_r<L><<<E.grid(eo ? 0 : 2), E.P.block, 0, st>>>(E.P.B, eo ? 0 : 2, eo ? S_BH : S_B, E.ra(FIN_RESID0));
+  // zero guess: r = source (bh or b); otherwise r = source - A x, recomputed
+  count_launch();
+  k_init_r<L, H><<<E.grid(eo ? 0 : 2), E.P.block, 0, st>>>(E.P.B, eo ? 0 : 2, eo ? S_BH : S_B, E.ra(FIN_RESID0));
+  if (profiler().timing) {
+    // host-stepped (profiled) run: launch the first FP64-class residual only
+    // when the guess is non-zero, so every timed launch does its work
+    static Flags* hf0 = nullptr;
+    if (!hf0) DW_CUDA(cudaMallocHost((void**)&hf0, sizeof(Flags)));
+    DW_CUDA(cudaMemcpyAsync(hf0, E.rb.flags, sizeof(Flags), cudaMemcpyDeviceToHost, st));
+    DW_CUDA(cudaStreamSynchronize(st));
+    if (hf0->rel_pending > 0) reliable(E, mode);
   } else {
-    count_launch();
-    k_init_r<L><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_B, E.ra(FIN_RESID0));
+    reliable(E, mode);
   }
-  reliable(E, mode);
   zstep(E, mode, FIN_GAMMA0);  // z, gamma
   count_launch();
   k_update_p<L><<<E.grid(eo ? 0 : 2), E.P.block, 0, st>>>(E.P.B, eo ? 0 : 2, E.ra(FIN_STORE0));  // p = z
@@ -372,23 +402,30 @@ dw_status CG<L, A, C12>::run(const SolveArgs& a) {
     DW_TRY(run_stepped(E, mode, a.p.maxiter));
   }
 
-  // ---- finish: odd sites, true residual, normal residual
+  // ---- finish: odd sites, then the IEEE FP64 residual from the caller's fields
   if (eo) {
-    hop<P64, P64, false, false>(E, 1, kLinkHi, InOne<P64>{S_X}, EpiXpay<P64, P64, C_PK, false>{S_X, S_B, G_ALL});
+    hop<H, H, false, false>(E, 1, kLinkHi, InOne<H>{S_X}, EpiXpay<H, H, C_PK, false>{S_X, S_B, G_ALL});
   }
+  if (H != P64) {
+    count_launch();
+    k_convert<P64, H><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_XU, S_X, E.ra(FIN_STORE0));
+  }
+  const int rt64 = H == P64 ? S_RT : S_AUX1;  // FP64 full temporary (verify_normal)
   if (mode != MODE_NORMAL) {
-    hop<P64, P64, false, false>(E, 2, kLinkHi, InOne<P64>{S_X}, EpiResidFull<L, false>{G_ALL, S_RT, S_X, S_B},
+    hop<P64, P64, false, false>(E, 2, S_LF64, InOne<P64>{S_XU},
+                                EpiResidFull<L, false, P64>{G_ALL, a.p.verify_normal ? rt64 : -1, S_XU, S_BU},
                                 FIN_STORE0);
     if (a.p.verify_normal) {
-      hop<P64, P64, false, true>(E, 2, kLinkHi, InOne<P64>{S_RT}, EpiXpay<P64, P64, C_MK, true>{-1, S_RT, G_ALL},
+      hop<P64, P64, false, true>(E, 2, S_LF64, InOne<P64>{rt64}, EpiXpay<P64, P64, C_MK, true>{-1, rt64, G_ALL},
                                  FIN_STORE1);
-      hop<P64, P64, false, true>(E, 2, kLinkHi, InOne<P64>{S_B}, EpiXpay<P64, P64, C_MK, true>{-1, S_B, G_ALL},
+      hop<P64, P64, false, true>(E, 2, S_LF64, InOne<P64>{S_BU}, EpiXpay<P64, P64, C_MK, true>{-1, S_BU, G_ALL},
                                  FIN_STORE2);
     }
   } else {
-    // |b - D^dag D x|^2
-    hop<P64, P64, false, false>(E, 2, kLinkHi, InOne<P64>{S_X}, EpiXpay<P64, P64, C_MK, false>{S_AUX0, S_X, G_ALL});
-    hop<P64, P64, false, true>(E, 2, kLinkHi, InOne<P64>{S_AUX0}, EpiResidFull<L, false>{G_ALL, S_RT, S_AUX0, S_B},
+    // |b - D^dag D x|^2 in FP64: t = D x into the FP64 temporary, then b - D^dag t
+    const int t64 = H == P64 ? S_AUX0 : S_AUX1;
+    hop<P64, P64, false, false>(E, 2, S_LF64, InOne<P64>{S_XU}, EpiXpay<P64, P64, C_MK, false>{t64, S_XU, G_ALL});
+    hop<P64, P64, false, true>(E, 2, S_LF64, InOne<P64>{t64}, EpiResidFull<L, false, P64>{G_ALL, -1, t64, S_BU},
                                FIN_STORE0);
   }
   DW_CUDA(cudaEventRecord(ev1, st));

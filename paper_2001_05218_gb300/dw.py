@@ -28,9 +28,9 @@ DW_OK, DW_ERR_ARG, DW_ERR_SHAPE, DW_ERR_PRECISION, DW_ERR_OOM, DW_ERR_CUDA, \
     DW_ERR_NOT_CONVERGED, DW_ERR_BREAKDOWN, DW_ERR_TIMEOUT = range(9)
 STATUS_NAMES = ["DW_OK", "DW_ERR_ARG", "DW_ERR_SHAPE", "DW_ERR_PRECISION", "DW_ERR_OOM", "DW_ERR_CUDA",
                 "DW_ERR_NOT_CONVERGED", "DW_ERR_BREAKDOWN", "DW_ERR_TIMEOUT"]
-DW_F64, DW_F32, DW_F16, DW_BF16 = range(4)
+DW_F64, DW_F32, DW_F16, DW_BF16, DW_DF64 = range(5)
 DW_GAUGE, DW_SPINOR_FULL, DW_SPINOR_EVEN, DW_SPINOR_ODD = range(4)
-PREC = {"f64": DW_F64, "f32": DW_F32, "f16": DW_F16, "bf16": DW_BF16}
+PREC = {"f64": DW_F64, "f32": DW_F32, "f16": DW_F16, "bf16": DW_BF16, "df64": DW_DF64}
 
 
 class dw_lattice(ctypes.Structure):
@@ -41,7 +41,7 @@ class dw_solver_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner", ctypes.c_int),
                 ("delta", ctypes.c_double), ("eo", ctypes.c_int), ("compress12", ctypes.c_int),
                 ("recompute_fwd", ctypes.c_int), ("tile", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("timeout_s", ctypes.c_double), ("verify_normal", ctypes.c_int)]
+                ("timeout_s", ctypes.c_double), ("verify_normal", ctypes.c_int), ("outer", ctypes.c_int)]
 
 
 class dw_profile_entry(ctypes.Structure):
@@ -147,7 +147,7 @@ def params(**kw) -> dw_solver_params:
     p = dw_solver_params()
     check(dw_solver_params_default(ctypes.byref(p)))
     for k, v in kw.items():
-        if k == "inner" and isinstance(v, str):
+        if k in ("inner", "outer") and isinstance(v, str):
             v = PREC[v]
         setattr(p, k, v)
     return p

@@ -42,20 +42,22 @@ def test_small_workload_full_lattice_fp64(dw):
     assert abs(st[0]["iters"] - it10) <= 2
 
 
-@pytest.mark.parametrize("inner,c12", [("f64", 0), ("f32", 0), ("f32", 1), ("f16", 1), ("bf16", 1), ("f16", 0)])
+@pytest.mark.parametrize("inner,c12,outer", [("f64", 0, "f64"), ("df64", 0, "f64"), ("f32", 0, "f64"),
+                                            ("f32", 1, "df64"), ("f16", 1, "f64"), ("f16", 1, "df64"),
+                                            ("bf16", 1, "df64"), ("f16", 0, "f64")])
 @pytest.mark.parametrize("eo", [1, 0])
-def test_mixed_solves_reach_fp64_residual(dw, inner, c12, eo):
+def test_mixed_solves_reach_fp64_residual(dw, inner, c12, outer, eo):
     dims, kappa = (8, 8, 8, 8), 0.122
     U = I.gauge_field(dims, "exp", 5, 1, 0.4)
     b = I.gaussian_spinor(dims, 5, 2)
     Ug = dw.gauge(dims, kappa, U)
     bg = dw.spinor(dims, b)
     x = dw.spinor(dims)
-    s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner=inner, compress12=c12, eo=eo))
+    s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner=inner, compress12=c12, eo=eo, outer=outer))
     assert s == dw.DW_OK
     assert st[0]["true_rel_resid"] <= 1e-10
     assert _resid(dims, kappa, U, x.download(), b) <= 1e-10
-    if inner != "f64":
+    if inner not in ("f64", "df64"):
         assert st[0]["reliable_updates"] >= 1
 
 
@@ -64,16 +66,18 @@ def test_medium_workload_eo_mixed_and_fp64(dw):
     Ug = dw.gauge(dims, kappa, U)
     bg = dw.spinor(dims, b)
     res = {}
-    for inner in ("f64", "f32"):
+    for inner, outer in (("f64", "f64"), ("f32", "f64"), ("f16", "df64")):
         x = dw.spinor(dims)
-        s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner=inner))
+        s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner=inner, outer=outer,
+                                                 compress12=1 if inner == "f16" else 0))
         assert s == dw.DW_OK and st[0]["true_rel_resid"] <= 1e-10
         xs = x.download()
         assert _resid(dims, kappa, U, xs, b) <= 1e-10
         res[inner] = (xs, st[0])
     # both solutions agree to the accuracy the residual bound allows
-    d = np.linalg.norm(res["f64"][0] - res["f32"][0]) / np.linalg.norm(res["f64"][0])
-    assert d < 1e-7
+    for k in ("f32", "f16"):
+        d = np.linalg.norm(res["f64"][0] - res[k][0]) / np.linalg.norm(res["f64"][0])
+        assert d < 1e-7
 
 
 def test_multi_rhs_point_sources(dw):
@@ -115,11 +119,13 @@ def test_normal_solve(dw):
     Ug = dw.gauge(dims, kappa, U)
     bg = dw.spinor(dims, b)
     x = dw.spinor(dims)
-    s, st = dw.cg_solve_normal(Ug, bg, x, dw.params(tol=1e-10, inner="f32"))
-    assert s == dw.DW_OK
-    xs = x.download()
-    r = np.linalg.norm(O.normal(dims, kappa, U, xs) - b) / np.linalg.norm(b)
-    assert r <= 1e-10
+    for outer in ("f64", "df64"):
+        x = dw.spinor(dims)
+        s, st = dw.cg_solve_normal(Ug, bg, x, dw.params(tol=1e-10, inner="f32", outer=outer))
+        assert s == dw.DW_OK
+        xs = x.download()
+        r = np.linalg.norm(O.normal(dims, kappa, U, xs) - b) / np.linalg.norm(b)
+        assert r <= 1e-10
 
 
 def test_not_converged_and_bad_source(dw):
