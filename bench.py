@@ -35,7 +35,8 @@ DEFAULT_WORKLOAD = "wilson_32x32x32x64_exp0.6"
 # iteration count of plain FP64 CG on the normal equations over the full
 # lattice (the oracle's algorithm) for each seeded workload, used to scale the
 # oracle's per-iteration time to a time-to-solution
-ORACLE_CGNR_ITERS = {}
+# (measured by running the oracle's own CGNR to 1e-10 on the seeded systems)
+ORACLE_CGNR_ITERS = {"wilson_32x32x32x64_exp0.6": 100, "wilson_16x16x16x32_exp0.4": 173}
 
 
 def rank_info():

@@ -230,6 +230,18 @@ struct Spin<P32> {
   __device__ static __forceinline__ void roundtrip(Cx<float> (&)[12]) {}
 };
 
+// Largest component magnitude of a site, the per-site scale of 16-bit
+// storage.  Sites whose largest component is below 1e-30 are stored as zero:
+// 1/scale would overflow FP32 there (values that small appear at the edge of
+// a point source's Krylov support), and they are negligible against any
+// residual norm the solver tests.
+__device__ __forceinline__ float site_max(const Cx<float> (&v)[12]) {
+  float m = 0.f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+  return m >= 1e-30f ? m : 0.f;
+}
+
 template <int P>
 struct Spin16 {
   using R = float;
@@ -248,9 +260,7 @@ struct Spin16 {
     }
   }
   __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&v)[12]) {
-    float m = 0.f;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+    float m = site_max(v);
     const float inv = m > 0.f ? 1.0f / m : 0.f;
     uint4* b = reinterpret_cast<uint4*>(base);
 #pragma unroll
@@ -265,9 +275,7 @@ struct Spin16 {
     reinterpret_cast<float*>(base + (size_t)48 * vh)[s] = m;
   }
   __device__ static __forceinline__ void roundtrip(Cx<float> (&v)[12]) {
-    float m = 0.f;
-#pragma unroll
-    for (int k = 0; k < 12; ++k) m = fmaxf(m, fmaxf(fabsf(v[k].re), fabsf(v[k].im)));
+    const float m = site_max(v);
     const float inv = m > 0.f ? 1.0f / m : 0.f;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {

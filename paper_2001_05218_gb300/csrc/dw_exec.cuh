@@ -3,6 +3,7 @@
 
 #include <cstdio>
 #include <string>
+#include <utility>
 
 #include "dw_internal.h"
 
@@ -63,6 +64,22 @@ struct Exec {
   }
   dim3 grid(int par_mode) const { return par_mode == 2 ? P.grid2 : P.grid1; }
 };
+
+// A solver plan kept across solves: launch plan with every field slot, the
+// working arena and the instantiated CUDA graph of the CG loop.
+struct SolveCacheEntry {
+  std::vector<unsigned long long> key;
+  Exec E;
+  char* arena = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int body_k = 0, rel_k = 0;
+  std::vector<std::pair<char*, size_t>> zero;  // ranges cleared at the start of every solve
+};
+// The entry with this key (moved to most recently used), or nullptr.
+SolveCacheEntry* solve_cache_find(const std::vector<unsigned long long>& key);
+// Inserts; evicts the least recently used entries beyond a small limit (after
+// synchronising the device).  The returned pointer stays valid until the next insert.
+SolveCacheEntry* solve_cache_insert(SolveCacheEntry&& e);
 
 template <int SPA, int LP, bool C12, bool DAG, class In, class Epi>
 inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int fin = FIN_STORE0) {

@@ -4,6 +4,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <list>
+#include <map>
+#include <sys/stat.h>
 #include <mutex>
 
 #include "dw_exec.cuh"
@@ -97,17 +100,18 @@ void geometry(SysDesc& S, const dw_lattice& l, int nrhs) {
   S.kappa = l.kappa;
 }
 
-void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T) {
+void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T, int RB) {
   memset(&P.B, 0, sizeof P.B);
   P.nsys = (int)lats.size();
   P.nrhs = nrhs;
-  int RB = 1;
-  if (nrhs > 1) {
-    T = 64;
-    for (int d = 4; d >= 1; --d)
-      if (nrhs % d == 0) { RB = d; break; }
-  } else if (T <= 0) {
+  if (T <= 0 || RB <= 0) {  // defaults: 128 sites per block, or 64 x (a divisor of nrhs up to 4)
+    RB = 1;
     T = 128;
+    if (nrhs > 1) {
+      T = 64;
+      for (int d = 4; d >= 1; --d)
+        if (nrhs % d == 0) { RB = d; break; }
+    }
   }
   P.B.nsys = P.nsys;
   P.B.T = T;
@@ -350,6 +354,85 @@ namespace dw {
 Profiler& profiler() {
   static Profiler p;
   return p;
+}
+
+// ------------------------------------------------------------------ autotuning cache
+static std::mutex g_tune_mu;
+static std::map<std::string, BlockShape>& tune_table() {
+  static std::map<std::string, BlockShape> t;
+  return t;
+}
+static std::string tune_path() {
+  const char* e = getenv("DW_TUNE_CACHE");
+  if (e && *e) return e;
+  const char* h = getenv("HOME");
+  return std::string(h ? h : "/tmp") + "/.cache/dwsolve/tune.txt";
+}
+static void tune_load_once() {
+  static bool loaded = false;
+  if (loaded) return;
+  loaded = true;
+  FILE* f = fopen(tune_path().c_str(), "r");
+  if (!f) return;
+  char key[512];
+  int T, RB;
+  while (fscanf(f, "%511s %d %d", key, &T, &RB) == 3)
+    if (T >= 32 && T <= 256 && T % 32 == 0 && RB >= 1 && T * RB <= 256) tune_table()[key] = BlockShape{T, RB};
+  fclose(f);
+}
+bool tune_lookup(const std::string& key, BlockShape* out) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_once();
+  auto it = tune_table().find(key);
+  if (it == tune_table().end()) return false;
+  *out = it->second;
+  return true;
+}
+void tune_store(const std::string& key, BlockShape v) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  tune_load_once();
+  tune_table()[key] = v;
+  const std::string path = tune_path();
+  const std::string dir = path.substr(0, path.find_last_of('/'));
+  std::string cmd_dir = dir;
+  // create the directory chain (best effort), then append
+  for (size_t pos = 1; pos < cmd_dir.size(); ++pos)
+    if (cmd_dir[pos] == '/') mkdir(cmd_dir.substr(0, pos).c_str(), 0755);
+  mkdir(cmd_dir.c_str(), 0755);
+  FILE* f = fopen(path.c_str(), "a");
+  if (f) {
+    fprintf(f, "%s %d %d\n", key.c_str(), v.T, v.RB);
+    fclose(f);
+  }
+}
+
+static constexpr size_t kSolveCacheMax = 4;
+static std::list<SolveCacheEntry>& solve_cache() {
+  static std::list<SolveCacheEntry> c;
+  return c;
+}
+
+SolveCacheEntry* solve_cache_find(const std::vector<unsigned long long>& key) {
+  auto& c = solve_cache();
+  for (auto it = c.begin(); it != c.end(); ++it)
+    if (it->key == key) {
+      c.splice(c.begin(), c, it);
+      return &c.front();
+    }
+  return nullptr;
+}
+
+SolveCacheEntry* solve_cache_insert(SolveCacheEntry&& e) {
+  auto& c = solve_cache();
+  c.push_front(std::move(e));
+  while (c.size() > kSolveCacheMax) {
+    SolveCacheEntry& old = c.back();
+    cudaDeviceSynchronize();
+    if (old.exec) cudaGraphExecDestroy(old.exec);
+    if (old.arena) cudaFree(old.arena);
+    c.pop_back();
+  }
+  return &c.front();
 }
 }  // namespace dw
 

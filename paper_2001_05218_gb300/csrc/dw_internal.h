@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <string>
 #include <vector>
 
 #include "dw.h"
@@ -78,7 +79,18 @@ struct Plan {
   int partials = 0;  // doubles in the partial-sum buffer
   dim3 block, grid1, grid2;  // one parity / both parities
 };
-void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T);
+// T sites per block and RB right-hand sides per block (T*RB <= 256, T a
+// multiple of 32); T <= 0 or RB <= 0 selects the defaults.
+void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T, int RB = 0);
+
+// Autotuned block shape (T, RB) for the inner stencil of a batch, cached per
+// (lattices, nrhs, storage, link compression, device) in memory and in the
+// file named by DW_TUNE_CACHE (default ~/.cache/dwsolve/tune.txt).
+struct BlockShape {
+  int T, RB;
+};
+bool tune_lookup(const std::string& key, BlockShape* out);
+void tune_store(const std::string& key, BlockShape v);
 
 // Device scratch for reductions of one plan.
 struct RedBuf {

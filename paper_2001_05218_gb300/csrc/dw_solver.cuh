@@ -30,6 +30,7 @@
 #include <chrono>
 
 #include "dw_exec.cuh"
+#include "dw_tune.cuh"
 
 namespace dw {
 
@@ -107,7 +108,8 @@ struct CG {
   }
 
   static dw_status run(const SolveArgs& a);
-  static dw_status run_graph(const Exec& E, int mode, int* body_kernels, int* rel_kernels);
+  static dw_status build_graph(const Exec& E, int mode, cudaGraphExec_t* exec, int* body_kernels,
+                               int* rel_kernels);
   static dw_status run_stepped(const Exec& E, int mode, int maxiter);
 };
 
@@ -136,7 +138,8 @@ struct CaptureStreams {
 // the loop is capped at maxiter + 2 passes, and every column also leaves the
 // loop through its own maxiter / timeout / breakdown checks.
 template <int L, int A, bool C12, int H>
-dw_status CG<L, A, C12, H>::run_graph(const Exec& E0, int mode, int* body_kernels, int* rel_kernels) {
+dw_status CG<L, A, C12, H>::build_graph(const Exec& E0, int mode, cudaGraphExec_t* exec, int* body_kernels,
+                                        int* rel_kernels) {
   static thread_local CaptureStreams cs;
   const int pm = mode == MODE_EO ? 0 : 2;
   cudaGraph_t g = nullptr;
@@ -156,7 +159,12 @@ dw_status CG<L, A, C12, H>::run_graph(const Exec& E0, int mode, int* body_kernel
 
   Exec E = E0;
   E.st = cs.a;
+  // count the captured kernel nodes (and never record profiling events into
+  // the graph: events cannot live inside conditional nodes)
   Profiler& pr = profiler();
+  const bool was_on = pr.on, was_timing = pr.timing;
+  pr.on = true;
+  pr.timing = false;
   const long long c0 = pr.launches;
   long long c1 = c0, c2 = c0;
   DW_CUDA(cudaStreamBeginCaptureToGraph(cs.a, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -197,15 +205,21 @@ dw_status CG<L, A, C12, H>::run_graph(const Exec& E0, int mode, int* body_kernel
   cudaGraph_t tmp;
   DW_CUDA(cudaStreamEndCapture(cs.a, &tmp));
   cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
-  if (e == cudaSuccess) e = cudaGraphLaunch(ge, E0.st);
-  if (ge) cudaGraphExecDestroy(ge);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) return cuda_error(e, "CG graph", __FILE__, __LINE__);
+  if (e != cudaSuccess) {
+    pr.on = was_on;
+    pr.timing = was_timing;
+    pr.launches = c0;
+    return cuda_error(e, "CG graph", __FILE__, __LINE__);
+  }
+  *exec = ge;
   // kernel nodes per pass of the loop body and of the reliable-update branch;
   // the executed counts are added once the device counters are read back
   *body_kernels = (int)((c1 - c0) + (pr.launches - c2));
   *rel_kernels = (int)(c2 - c1);
   pr.launches = c0;
+  pr.on = was_on;
+  pr.timing = was_timing;
   return DW_OK;
 }
 
@@ -236,11 +250,6 @@ dw_status CG<L, A, C12, H>::run_stepped(const Exec& E, int mode, int maxiter) {
   return DW_OK;
 }
 
-// Bytes of one even-odd spinor block in each role, per system and rhs.
-struct Arena {
-  char* base = nullptr;
-  size_t bytes = 0;
-};
 
 template <int L, int A, bool C12, int H>
 dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
@@ -251,79 +260,105 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
   const int fpar = eo ? 1 : 2;  // parities held by the inner vectors
   cudaStream_t st = a.st;
 
-  Exec E;
-  E.st = st;
   std::vector<dw_lattice> lats;
   for (int i = 0; i < n; ++i) lats.push_back(a.U[i]->lat);
-  make_plan(E.P, lats, nrhs, a.p.tile);
 
-  // ---- per-system arena layout (256-byte aligned pieces)
-  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  std::vector<size_t> off(n + 1, 0);
-  struct Piece { int slot, prec, npar; };
-  std::vector<Piece> pieces;
-  if (eo) {
-    pieces = {{S_BH, H, 1}, {S_RT, H, 2}, {S_XL, A, 1}, {S_R, L, 1},
-              {S_P, L, 1},  {S_Z, L, 1},  {S_W, L, 1},  {S_T, L, 1}};
-  } else if (mode == MODE_FULL) {
-    pieces = {{S_RT, H, 2}, {S_XL, A, 2}, {S_R, L, 2}, {S_P, L, 2}, {S_Z, L, 2}, {S_W, L, 2}};
-  } else {
-    pieces = {{S_RT, H, 2}, {S_AUX0, H, 2}, {S_XL, A, 2}, {S_R, L, 2},
-              {S_P, L, 2},  {S_W, L, 2},    {S_T, L, 2}};
-  }
-  if (H != P64) {  // high-precision copies of the caller's x and b
-    pieces.push_back({S_X, H, 2});
-    pieces.push_back({S_B, H, 2});
-  }
-  // FP64 full temporary for the certification (the FP64 arena piece doubles as it when H = FP64)
-  if ((a.p.verify_normal && H != P64) || (mode == MODE_NORMAL && H != P64)) pieces.push_back({S_AUX1, DW_F64, 2});
-  size_t total = 0;
-  std::vector<std::vector<size_t>> poff(n);
+  // ---- plan, arena and graph: reused from the cache when every pointer,
+  // shape and choice baked into them is the same
+  std::vector<const char*> lo_links(n), hi_links(n);
   for (int i = 0; i < n; ++i) {
-    const long long vh = vh_of(lats[i]);
-    for (auto& pc : pieces) {
-      poff[i].push_back(total);
-      total += al((size_t)nrhs * pc.npar * spin_bytes(pc.prec) * vh);
+    DW_TRY(derived_links(a.U[i], L, C12 ? 1 : 0, st, &lo_links[i]));
+    DW_TRY(derived_links(a.U[i], H, 0, st, &hi_links[i]));
+  }
+  std::vector<unsigned long long> key = {0xC6ull, (unsigned long long)L, (unsigned long long)A, C12 ? 1ull : 0ull,
+                                         (unsigned long long)H, (unsigned long long)mode, (unsigned long long)nrhs,
+                                         (unsigned long long)a.p.tile, (unsigned long long)a.p.verify_normal,
+                                         (unsigned long long)n};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  key.push_back((unsigned long long)dev);
+  for (int i = 0; i < n; ++i) {
+    unsigned long long kb;
+    memcpy(&kb, &lats[i].kappa, sizeof kb);
+    for (unsigned long long v :
+         {(unsigned long long)(uintptr_t)a.U[i]->ptr, (unsigned long long)(uintptr_t)lo_links[i],
+          (unsigned long long)(uintptr_t)hi_links[i], (unsigned long long)(uintptr_t)a.b[i]->ptr,
+          (unsigned long long)(uintptr_t)a.x[i]->ptr, (unsigned long long)lats[i].dims[0],
+          (unsigned long long)lats[i].dims[1], (unsigned long long)lats[i].dims[2],
+          (unsigned long long)lats[i].dims[3], kb, (unsigned long long)lats[i].t_antiperiodic})
+      key.push_back(v);
+  }
+  SolveCacheEntry* ent = solve_cache_find(key);
+  if (ent == nullptr) {
+    SolveCacheEntry fresh;
+    fresh.key = key;
+    Exec& F = fresh.E;
+    BlockShape shape{a.p.tile, a.p.tile > 0 ? 1 : 0};
+    if (a.p.tile <= 0) shape = tune_inner_shape<L, C12>(lats, nrhs, lo_links, st);
+    make_plan(F.P, lats, nrhs, shape.T, shape.RB);
+    auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+    struct Piece { int slot, prec, npar; };
+    std::vector<Piece> pieces;
+    if (eo) {
+      pieces = {{S_BH, H, 1}, {S_RT, H, 2}, {S_XL, A, 1}, {S_R, L, 1},
+                {S_P, L, 1},  {S_Z, L, 1},  {S_W, L, 1},  {S_T, L, 1}};
+    } else if (mode == MODE_FULL) {
+      pieces = {{S_RT, H, 2}, {S_XL, A, 2}, {S_R, L, 2}, {S_P, L, 2}, {S_Z, L, 2}, {S_W, L, 2}};
+    } else {
+      pieces = {{S_RT, H, 2}, {S_AUX0, H, 2}, {S_XL, A, 2}, {S_R, L, 2},
+                {S_P, L, 2},  {S_W, L, 2},    {S_T, L, 2}};
     }
+    if (H != P64) {  // high-precision copies of the caller's x and b
+      pieces.push_back({S_X, H, 2});
+      pieces.push_back({S_B, H, 2});
+    }
+    // FP64 full temporary for the certification (the FP64 arena pieces serve when H = FP64)
+    if (H != P64 && (a.p.verify_normal || mode == MODE_NORMAL)) pieces.push_back({S_AUX1, DW_F64, 2});
+    size_t total = 0;
+    std::vector<std::vector<size_t>> poff(n);
+    for (int i = 0; i < n; ++i) {
+      const long long vh = vh_of(lats[i]);
+      for (auto& pc : pieces) {
+        poff[i].push_back(total);
+        total += al((size_t)nrhs * pc.npar * spin_bytes(pc.prec) * vh);
+      }
+    }
+    const size_t red_bytes = al(sizeof(double) * F.P.partials) + al(sizeof(int) * kMaxSys) +
+                             al(sizeof(ColState) * F.P.ncols) + al(sizeof(Flags));
+    DW_CUDA(cudaMalloc((void**)&fresh.arena, total + red_bytes));
+    char* rp = fresh.arena + total;
+    F.rb.partial = reinterpret_cast<double*>(rp);
+    rp += al(sizeof(double) * F.P.partials);
+    F.rb.counter = reinterpret_cast<int*>(rp);
+    rp += al(sizeof(int) * kMaxSys);
+    F.rb.cols = reinterpret_cast<ColState*>(rp);
+    rp += al(sizeof(ColState) * F.P.ncols);
+    F.rb.flags = reinterpret_cast<Flags*>(rp);
+    for (int i = 0; i < n; ++i) {
+      SysDesc& S = F.P.B.sd[i];
+      S.f[S_LLO] = gauge_slot(lo_links[i], lats[i], L, C12 ? 1 : 0);
+      S.f[S_LHI] = gauge_slot(hi_links[i], lats[i], H, 0);
+      S.f[S_LF64] = gauge_slot(a.U[i]->ptr, lats[i], DW_F64, 0);
+      S.f[S_BU] = spinor_slot(a.b[i]);
+      S.f[S_XU] = spinor_slot(a.x[i]);
+      S.f[S_B] = S.f[S_BU];
+      S.f[S_X] = S.f[S_XU];
+      for (size_t k = 0; k < pieces.size(); ++k)
+        S.f[pieces[k].slot] = arena_slot(fresh.arena + poff[i][k], lats[i], pieces[k].prec, nrhs, pieces[k].npar);
+      if (mode == MODE_NORMAL) S.f[S_Z] = S.f[S_R];
+      for (auto pc : {S_XL, S_P})
+        fresh.zero.push_back({S.f[pc].p, (size_t)nrhs * fpar * (pc == S_XL ? spin_bytes(A) : spin_bytes(L)) * S.vh});
+    }
+    F.st = st;
+    dw_status gs = build_graph(F, mode, &fresh.exec, &fresh.body_k, &fresh.rel_k);
+    if (gs != DW_OK) {
+      cudaFree(fresh.arena);
+      return gs;
+    }
+    ent = solve_cache_insert(std::move(fresh));
   }
-  const size_t red_bytes = al(sizeof(double) * E.P.partials) + al(sizeof(int) * kMaxSys) +
-                           al(sizeof(ColState) * E.P.ncols) + al(sizeof(Flags));
-  char* arena = nullptr;
-  DW_CUDA(cudaMallocAsync((void**)&arena, total + red_bytes, st));
-  char* rp = arena + total;
-  E.rb.partial = reinterpret_cast<double*>(rp);
-  rp += al(sizeof(double) * E.P.partials);
-  E.rb.counter = reinterpret_cast<int*>(rp);
-  rp += al(sizeof(int) * kMaxSys);
-  E.rb.cols = reinterpret_cast<ColState*>(rp);
-  rp += al(sizeof(ColState) * E.P.ncols);
-  E.rb.flags = reinterpret_cast<Flags*>(rp);
-
-  // ---- slots
-  dw_status status = DW_OK;
-  for (int i = 0; i < n && status == DW_OK; ++i) {
-    SysDesc& S = E.P.B.sd[i];
-    const char* lo = nullptr;
-    status = derived_links(a.U[i], L, C12 ? 1 : 0, st, &lo);
-    if (status != DW_OK) break;
-    S.f[S_LLO] = gauge_slot(lo, lats[i], L, C12 ? 1 : 0);
-    const char* hi = nullptr;
-    status = derived_links(a.U[i], H, 0, st, &hi);
-    if (status != DW_OK) break;
-    S.f[S_LHI] = gauge_slot(hi, lats[i], H, 0);
-    S.f[S_LF64] = gauge_slot(a.U[i]->ptr, lats[i], DW_F64, 0);
-    S.f[S_BU] = spinor_slot(a.b[i]);
-    S.f[S_XU] = spinor_slot(a.x[i]);
-    S.f[S_B] = S.f[S_BU];
-    S.f[S_X] = S.f[S_XU];
-    for (size_t k = 0; k < pieces.size(); ++k)
-      S.f[pieces[k].slot] = arena_slot(arena + poff[i][k], lats[i], pieces[k].prec, nrhs, pieces[k].npar);
-    if (mode == MODE_NORMAL) S.f[S_Z] = S.f[S_R];
-  }
-  if (status != DW_OK) {
-    cudaFreeAsync(arena, st);
-    return status;
-  }
+  Exec E = ent->E;
+  E.st = st;
 
   // ---- column state
   std::vector<ColState> hc(E.P.ncols);
@@ -363,13 +398,7 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
     count_launch();
     k_convert<H, P64><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_X, S_XU, E.ra(FIN_STORE0));
   }
-  for (int i = 0; i < n; ++i) {
-    const SysDesc& S = E.P.B.sd[i];
-    for (auto pc : {S_XL, S_P}) {
-      const size_t nb = (size_t)nrhs * fpar * (pc == S_XL ? spin_bytes(A) : spin_bytes(L)) * S.vh;
-      DW_CUDA(cudaMemsetAsync(S.f[pc].p, 0, nb, st));
-    }
-  }
+  for (auto& z : ent->zero) DW_CUDA(cudaMemsetAsync(z.first, 0, z.second, st));
   if (eo) {
     // bh = b_e + kappa H_eo b_o
     hop<H, H, false, false>(E, 0, kLinkHi, InOne<H>{S_B}, EpiXpay<H, H, C_PK, false>{S_BH, S_B, G_ALL});
@@ -394,10 +423,10 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
   DW_CUDA(cudaGetLastError());
 
   // ---- iterations
-  int body_k = 0, rel_k = 0;
+  const int body_k = ent->body_k, rel_k = ent->rel_k;
   const bool graph = !profiler().timing;
   if (graph) {
-    DW_TRY(run_graph(E, mode, &body_k, &rel_k));
+    DW_CUDA(cudaGraphLaunch(ent->exec, st));
   } else {
     DW_TRY(run_stepped(E, mode, a.p.maxiter));
   }
@@ -431,7 +460,6 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
   DW_CUDA(cudaEventRecord(ev1, st));
   DW_CUDA(cudaMemcpyAsync(hc.data(), E.rb.cols, sizeof(ColState) * hc.size(), cudaMemcpyDeviceToHost, st));
   DW_CUDA(cudaMemcpyAsync(&hf, E.rb.flags, sizeof hf, cudaMemcpyDeviceToHost, st));
-  cudaFreeAsync(arena, st);
   DW_CUDA(cudaStreamSynchronize(st));
   if (graph && profiler().on) profiler().launches += (long long)hf.loops * body_k + (long long)hf.rel_runs * rel_k;
   float ms = 0.f;
