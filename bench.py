@@ -104,11 +104,13 @@ class ClockSampler:
 
 
 def source_hash():
+    """Hash of the files that define the stencil kernel (storage formats and
+    the kernel template): a DRAM-traffic figure is only reported for the
+    kernel it was measured on."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2001_05218_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in ("dw_common.cuh", "dw_kernels.cuh"):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -406,8 +408,22 @@ def main():
             e2e_step()
         barrier()
         e2e_s = (time.perf_counter() - a0) / ne
+        # one more step with events between the phases (stream time)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        evs[0].record(stream)
+        dw.check(dw.dw_field_upload(Ug.handle, ctypes.c_void_p(Uh.data_ptr()), sp))
+        evs[1].record(stream)
+        dw.check(dw.dw_field_upload(bg.handle, ctypes.c_void_p(bh.data_ptr()), sp))
+        evs[2].record(stream)
+        reset_x()
+        dw.cg_solve(Ug, bg, xg, p_mix)
+        evs[3].record(stream)
+        dw.check(dw.dw_field_download(xg.handle, ctypes.c_void_p(xh.data_ptr()), sp))
+        evs[4].record(stream)
+        torch.cuda.synchronize()
+        phases = {k: evs[i].elapsed_time(evs[i + 1]) for i, k in enumerate(["upload_U", "upload_b", "solve", "download_x"])}
         e2e = {"value": world / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": int(Uh.numel() * 8 + bh.numel() * 8),
-               "d2h_bytes_per_step": int(xh.numel() * 8), "ms_per_step": e2e_s * 1e3}
+               "d2h_bytes_per_step": int(xh.numel() * 8), "ms_per_step": e2e_s * 1e3, "phases_ms": phases}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:

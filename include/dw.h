@@ -110,13 +110,16 @@ dw_status dw_field_wrap(const dw_lattice* lat, dw_kind kind, dw_prec prec, int c
 dw_status dw_field_free(dw_field* f);
 
 /* Copy host canonical complex128 data into the field (converted to the
- * field's storage precision and layout).  `host` may be pageable or pinned;
- * with pinned memory the copy is asynchronous on `stream` and the host buffer
- * must stay valid until the stream reaches this point. */
+ * field's storage precision and layout).  `host` may be pageable or pinned.
+ * Pinned (page-locked) memory is read directly by the layout kernel over the
+ * host link, asynchronously on `stream`: the buffer must stay valid and
+ * unchanged until the stream reaches this point.  Pageable memory is staged
+ * through a device buffer. */
 dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream);
 
-/* Copy the field back to host canonical complex128.  Data are valid once
- * `stream` has been synchronised. */
+/* Copy the field back to host canonical complex128 (pinned memory is written
+ * directly by the layout kernel).  Data are valid once `stream` has been
+ * synchronised. */
 dw_status dw_field_download(const dw_field* f, double* host, dw_stream_t stream);
 
 /* As upload/download, with the canonical complex128 array in device memory. */

@@ -39,10 +39,20 @@ def _newest_header() -> float:
 
 
 def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | None = None) -> str:
+    """extra (or the DW_EXTRA_NVCC environment variable) adds nvcc flags; a
+    change of flags rebuilds every object."""
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
+    extra = list(extra or []) + os.environ.get("DW_EXTRA_NVCC", "").split()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr = _newest_header()
+    stamp = os.path.join(BUILD, "flags.txt")
+    flags_now = " ".join(ARCH + FLAGS + extra)
+    if not os.path.exists(stamp) or open(stamp).read() != flags_now:
+        for o in glob.glob(os.path.join(BUILD, "*.o")):
+            os.remove(o)
+        with open(stamp, "w") as f:
+            f.write(flags_now)
     todo = []
     objs = []
     for s in srcs:
@@ -53,7 +63,7 @@ def build(verbose: bool = False, jobs: int | None = None, extra: list[str] | Non
 
     def comp(so):
         s, o = so
-        cmd = [cc] + ARCH + FLAGS + (extra or []) + ["-c", s, "-o", o + ".tmp"]
+        cmd = [cc] + ARCH + FLAGS + extra + ["-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s%s" % (s, r.stdout, r.stderr))

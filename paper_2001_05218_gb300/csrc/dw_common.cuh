@@ -190,6 +190,7 @@ struct Spin;
 template <>
 struct Spin<P64> {
   using R = double;
+  static constexpr bool kScaled = false;
   static constexpr int kBytes = 192;  // bytes per site
   __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<double> (&v)[12]) {
     const double2* b = reinterpret_cast<const double2*>(base);
@@ -211,6 +212,7 @@ struct Spin<P64> {
 template <>
 struct Spin<P32> {
   using R = float;
+  static constexpr bool kScaled = false;
   static constexpr int kBytes = 96;
   __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&v)[12]) {
     const float4* b = reinterpret_cast<const float4*>(base);
@@ -245,7 +247,22 @@ __device__ __forceinline__ float site_max(const Cx<float> (&v)[12]) {
 template <int P>
 struct Spin16 {
   using R = float;
+  static constexpr bool kScaled = true;
   static constexpr int kBytes = 52;  // 48 bytes of halves + 4 bytes of scale
+  // stored values (unscaled) and the site's scale: value = v * scale
+  __device__ static __forceinline__ void load_raw(const char* base, int vh, int s, Cx<float> (&v)[12], float& sc) {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+    sc = __ldg(reinterpret_cast<const float*>(base + (size_t)48 * vh) + s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint4 t = __ldg(b + (size_t)k * vh + s);
+      float2 a = H16<P>::to2(t.x), c = H16<P>::to2(t.y), d = H16<P>::to2(t.z), e = H16<P>::to2(t.w);
+      v[4 * k + 0] = cx(a.x, a.y);
+      v[4 * k + 1] = cx(c.x, c.y);
+      v[4 * k + 2] = cx(d.x, d.y);
+      v[4 * k + 3] = cx(e.x, e.y);
+    }
+  }
   __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&v)[12]) {
     const uint4* b = reinterpret_cast<const uint4*>(base);
     const float sc = __ldg(reinterpret_cast<const float*>(base + (size_t)48 * vh) + s);
@@ -293,6 +310,7 @@ struct Spin<PB16> : Spin16<PB16> {};
 template <>
 struct Spin<PDF> {
   using R = DF;
+  static constexpr bool kScaled = false;
   static constexpr int kBytes = 192;
   __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<DF> (&v)[12]) {
     const float4* b = reinterpret_cast<const float4*>(base);
@@ -499,8 +517,20 @@ enum SlotId {
   kNumSlots
 };
 
+// Unsigned division by an invariant divisor d < 2^31 (Granlund & Montgomery
+// 1994, branch-free form): q = (t + ((n - t) >> s1)) >> s2, t = umulhi(m, n).
+struct FastDiv {
+  unsigned m;
+  int s1, s2;
+};
+__device__ __forceinline__ int fdiv(int n, FastDiv f) {
+  const unsigned t = __umulhi(f.m, (unsigned)n);
+  return (int)((t + (((unsigned)n - t) >> f.s1)) >> f.s2);
+}
+
 struct SysDesc {
   int lxh, ly, lz, lt;  // Lx/2, Ly, Lz, Lt
+  FastDiv div_lxh, div_ly, div_lz;
   int vh;               // sites per parity
   int nrhs;
   int anti_t;

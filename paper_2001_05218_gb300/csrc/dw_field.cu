@@ -88,12 +88,25 @@ Slot gauge_slot(const char* p, const dw_lattice& l, int prec, int c12) {
   return s;
 }
 
+static FastDiv fast_div(int d) {
+  int l = 0;
+  while ((1ll << l) < d) ++l;
+  FastDiv f;
+  f.m = (unsigned)((((unsigned long long)1 << 32) * ((1ull << l) - (unsigned long long)d)) / (unsigned long long)d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l - 1 > 0 ? l - 1 : 0;
+  return f;
+}
+
 void geometry(SysDesc& S, const dw_lattice& l, int nrhs) {
   memset(&S, 0, sizeof S);
   S.lxh = l.dims[0] / 2;
   S.ly = l.dims[1];
   S.lz = l.dims[2];
   S.lt = l.dims[3];
+  S.div_lxh = fast_div(S.lxh);
+  S.div_ly = fast_div(S.ly);
+  S.div_lz = fast_div(S.lz);
   S.vh = (int)vh_of(l);
   S.nrhs = nrhs;
   S.anti_t = l.t_antiperiodic ? 1 : 0;
@@ -154,17 +167,33 @@ struct Dims4 {
   int d[4];
 };
 
-// canonical (complex128, [rhs][site][12]) -> storage; full: site = lex, parity
-// field: site = j.  One thread per (parity, j), loop over rhs.
+// canonical (complex128, [rhs][site][12]) <-> storage.  Threads run over the
+// canonical site order (lexicographic for full fields, j for parity fields) so
+// that a warp touches one contiguous stretch of the canonical array -- which
+// may be page-locked host memory read or written over the host link.
+__host__ __device__ inline void site_to_eo(const int* d, long long lex, int* par, long long* j) {
+  long long q = lex / d[0];
+  const int x = (int)(lex - q * d[0]);
+  const int y = (int)(q % d[1]);
+  q /= d[1];
+  const int z = (int)(q % d[2]);
+  const int t = (int)(q / d[2]);
+  *par = (x + y + z + t) & 1;
+  *j = lex >> 1;
+}
+
 template <int P>
 __global__ void k_pack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, const double2* __restrict__ can,
                               Slot dst) {
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int pi = blockIdx.y;  // parity index within the field
-  if (j >= vh) return;
-  const int par = npar == 2 ? pi : par0;
-  const long long site = npar == 2 ? lex_of(dm.d, par, j) : j;
+  const long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nsite = (long long)vh * npar;
+  if (site >= nsite) return;
+  int par = par0, pi = 0;
+  long long j = site;
+  if (npar == 2) {
+    site_to_eo(dm.d, site, &par, &j);
+    pi = par;
+  }
   using R = typename Spin<P>::R;
   for (int r = 0; r < nrhs; ++r) {
     const double2* src = can + ((long long)r * nsite + site) * 12;
@@ -180,12 +209,15 @@ __global__ void k_pack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, co
 
 template <int P>
 __global__ void k_unpack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, Slot srcs, double2* __restrict__ can) {
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int pi = blockIdx.y;
-  if (j >= vh) return;
-  const int par = npar == 2 ? pi : par0;
-  const long long site = npar == 2 ? lex_of(dm.d, par, j) : j;
+  const long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nsite = (long long)vh * npar;
+  if (site >= nsite) return;
+  int par = par0, pi = 0;
+  long long j = site;
+  if (npar == 2) {
+    site_to_eo(dm.d, site, &par, &j);
+    pi = par;
+  }
   using R = typename Spin<P>::R;
   for (int r = 0; r < nrhs; ++r) {
     Cx<R> v[12];
@@ -198,10 +230,11 @@ __global__ void k_unpack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, 
 
 template <int P, bool C12>
 __global__ void k_pack_gauge(Dims4 dm, int vh, const double2* __restrict__ can, char* dst) {
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int par = blockIdx.y;
-  if (j >= vh) return;
-  const long long site = lex_of(dm.d, par, j);
+  const long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (site >= 2ll * vh) return;
+  int par;
+  long long j;
+  site_to_eo(dm.d, site, &par, &j);
   const long long lb = (long long)Link<P, C12>::kBytes * vh;
   using R = typename Link<P, C12>::R;
   for (int mu = 0; mu < 4; ++mu) {
@@ -218,10 +251,11 @@ __global__ void k_pack_gauge(Dims4 dm, int vh, const double2* __restrict__ can, 
 
 template <int P, bool C12>
 __global__ void k_unpack_gauge(Dims4 dm, int vh, const char* src, double2* __restrict__ can) {
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int par = blockIdx.y;
-  if (j >= vh) return;
-  const long long site = lex_of(dm.d, par, j);
+  const long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (site >= 2ll * vh) return;
+  int par;
+  long long j;
+  site_to_eo(dm.d, site, &par, &j);
   const long long lb = (long long)Link<P, C12>::kBytes * vh;
   using R = typename Link<P, C12>::R;
   for (int mu = 0; mu < 4; ++mu) {
@@ -269,7 +303,7 @@ dw_status pack_spinor_from_canonical(dw_field* f, const double* dev, cudaStream_
   const int vh = (int)vh_of(f->lat);
   const int npar = npar_of(f->kind);
   const int par0 = f->kind == DW_SPINOR_ODD ? 1 : 0;
-  dim3 b(256), g((vh + 255) / 256, npar);
+  dim3 b(256), g((unsigned)(((long long)vh * npar + 255) / 256));
   Slot s = spinor_slot(f);
   const double2* c = reinterpret_cast<const double2*>(dev);
   DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_spinor<PP><<<g, b, 0, st>>>(dims4(f->lat), vh, f->nrhs, npar, par0, c, s)));
@@ -281,7 +315,7 @@ dw_status unpack_spinor_to_canonical(const dw_field* f, double* dev, cudaStream_
   const int vh = (int)vh_of(f->lat);
   const int npar = npar_of(f->kind);
   const int par0 = f->kind == DW_SPINOR_ODD ? 1 : 0;
-  dim3 b(256), g((vh + 255) / 256, npar);
+  dim3 b(256), g((unsigned)(((long long)vh * npar + 255) / 256));
   Slot s = spinor_slot(f);
   double2* c = reinterpret_cast<double2*>(dev);
   DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_spinor<PP><<<g, b, 0, st>>>(dims4(f->lat), vh, f->nrhs, npar, par0, s, c)));
@@ -291,7 +325,7 @@ dw_status unpack_spinor_to_canonical(const dw_field* f, double* dev, cudaStream_
 
 static dw_status pack_gauge(dw_field* f, const double* dev, cudaStream_t st) {
   const int vh = (int)vh_of(f->lat);
-  dim3 b(256), g((vh + 255) / 256, 2);
+  dim3 b(256), g((unsigned)((2ll * vh + 255) / 256));
   const double2* c = reinterpret_cast<const double2*>(dev);
   if (f->compress12) {
     DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_gauge<PP, true><<<g, b, 0, st>>>(dims4(f->lat), vh, c, f->ptr)));
@@ -304,7 +338,7 @@ static dw_status pack_gauge(dw_field* f, const double* dev, cudaStream_t st) {
 
 static dw_status unpack_gauge(const dw_field* f, double* dev, cudaStream_t st) {
   const int vh = (int)vh_of(f->lat);
-  dim3 b(256), g((vh + 255) / 256, 2);
+  dim3 b(256), g((unsigned)((2ll * vh + 255) / 256));
   double2* c = reinterpret_cast<double2*>(dev);
   if (f->compress12) {
     DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_gauge<PP, true><<<g, b, 0, st>>>(dims4(f->lat), vh, f->ptr, c)));
@@ -587,9 +621,21 @@ dw_status dw_field_export(const dw_field* f, double* dev, dw_stream_t stream) {
   return unpack_spinor_to_canonical(f, dev, st);
 }
 
+// Device-visible address of page-locked host memory (NULL for pageable memory).
+static const void* pinned_device_ptr(const void* host) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream) {
   DW_CHECK(f != nullptr && host != nullptr, DW_ERR_ARG, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // pinned memory: the layout kernel reads the host array directly
+  if (const void* dp = pinned_device_ptr(host)) return dw_field_import(f, static_cast<const double*>(dp), stream);
   const size_t nb = canonical_bytes(f);
   void* tmp = nullptr;
   DW_CUDA(cudaMallocAsync(&tmp, nb, st));
@@ -602,6 +648,8 @@ dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream) {
 dw_status dw_field_download(const dw_field* f, double* host, dw_stream_t stream) {
   DW_CHECK(f != nullptr && host != nullptr, DW_ERR_ARG, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (const void* dp = pinned_device_ptr(host))
+    return dw_field_export(f, static_cast<double*>(const_cast<void*>(dp)), stream);
   const size_t nb = canonical_bytes(f);
   void* tmp = nullptr;
   DW_CUDA(cudaMallocAsync(&tmp, nb, st));

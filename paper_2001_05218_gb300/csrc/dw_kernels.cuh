@@ -84,6 +84,35 @@ __device__ __forceinline__ void accumulate(Cx<R> (&acc)[12], const Cx<R> (&g)[6]
   }
 }
 
+// acc + w * g  (w real), componentwise FMA
+template <typename R>
+__device__ __forceinline__ Cx<R> cfma(R w, Cx<R> g, Cx<R> acc) { return cx(fma(w, g.re, acc.re), fma(w, g.im, acc.im)); }
+
+// acc += w (1 + S gamma_mu) reconstructed from g, w = dequantisation scale times
+// the boundary sign (the 16-bit inputs are projected and multiplied unscaled)
+template <int MU, int S, typename R>
+__device__ __forceinline__ void accumulate_w(Cx<R> (&acc)[12], const Cx<R> (&g)[6], R w) {
+  const R ws = S > 0 ? w : -w;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc[c] = cfma(w, g[c], acc[c]);
+    acc[3 + c] = cfma(w, g[3 + c], acc[3 + c]);
+    if (MU == 0) {        // lower = S i (g1, g0)
+      acc[6 + c] = cfma(ws, mul_i(g[3 + c]), acc[6 + c]);
+      acc[9 + c] = cfma(ws, mul_i(g[c]), acc[9 + c]);
+    } else if (MU == 1) { // lower = S (g1, -g0)
+      acc[6 + c] = cfma(ws, g[3 + c], acc[6 + c]);
+      acc[9 + c] = cfma(-ws, g[c], acc[9 + c]);
+    } else if (MU == 2) { // lower = S i (g0, -g1)
+      acc[6 + c] = cfma(ws, mul_i(g[c]), acc[6 + c]);
+      acc[9 + c] = cfma(-ws, mul_i(g[3 + c]), acc[9 + c]);
+    } else {              // lower = S (g0, g1)
+      acc[6 + c] = cfma(ws, g[c], acc[6 + c]);
+      acc[9 + c] = cfma(ws, g[3 + c], acc[9 + c]);
+    }
+  }
+}
+
 // g = U h (ADJ = false) or U^dag h (ADJ = true), on both half-spinor spins
 template <bool ADJ, typename R>
 __device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6], Cx<R> (&g)[6]) {
@@ -194,13 +223,13 @@ struct Coord {
 
 __device__ __forceinline__ Coord coord_of(const SysDesc& S, int s, int par) {
   Coord c;
-  int q = s / S.lxh;
+  int q = fdiv(s, S.div_lxh);
   c.xh = s - q * S.lxh;
   c.row = s - c.xh;
-  c.y = q % S.ly;
-  q /= S.ly;
-  c.z = q % S.lz;
-  c.t = q / S.lz;
+  int q2 = fdiv(q, S.div_ly);
+  c.y = q - q2 * S.ly;
+  c.t = fdiv(q2, S.div_lz);
+  c.z = q2 - c.t * S.lz;
   c.x = 2 * c.xh + ((c.y + c.z + c.t + par) & 1);
   return c;
 }
@@ -269,7 +298,7 @@ __device__ __forceinline__ void convert12(const Cx<Q> (&a)[12], Cx<R> (&b)[12]) 
 template <int SP>
 struct InOne {
   int slot;
-  static const char* name() { return "one"; }
+  static constexpr bool kScaled = Spin<SP>::kScaled;
   __host__ double io_bytes() const { return Spin<SP>::kBytes; }
   template <typename R>
   __device__ __forceinline__ void load(const SysDesc& S, int par, int r, int s, Cx<R> (&v)[12]) const {
@@ -277,12 +306,23 @@ struct InOne {
     Spin<SP>::load(slot_ptr(S, slot, r, par), S.vh, s, t);
     convert12(t, v);
   }
+  // 16-bit storage: unscaled values and the site scale
+  template <typename R>
+  __device__ __forceinline__ void load_raw(const SysDesc& S, int par, int r, int s, Cx<R> (&v)[12], R& sc) const {
+    if constexpr (Spin<SP>::kScaled) {
+      Spin<SP>::load_raw(slot_ptr(S, slot, r, par), S.vh, s, v, sc);
+    } else {
+      load(S, par, r, s, v);
+      sc = (R)1;
+    }
+  }
 };
 
 // Neighbour spinor x + xl: the high-precision accumulator plus the
 // low-precision increment.
 template <int SPH, int SPL>
 struct InSum {
+  static constexpr bool kScaled = false;
   int slot_x, slot_xl;
   __host__ double io_bytes() const { return Spin<SPH>::kBytes + Spin<SPL>::kBytes; }
   template <typename R>
@@ -294,6 +334,11 @@ struct InSum {
     Spin<SPL>::load(slot_ptr(S, slot_xl, r, par), S.vh, s, b);
 #pragma unroll
     for (int k = 0; k < 12; ++k) v[k] = cx((R)(a[k].re + (RH)b[k].re), (R)(a[k].im + (RH)b[k].im));
+  }
+  template <typename R>
+  __device__ __forceinline__ void load_raw(const SysDesc& S, int par, int r, int s, Cx<R> (&v)[12], R& sc) const {
+    load(S, par, r, s, v);
+    sc = (R)1;
   }
 };
 
@@ -461,9 +506,20 @@ struct EpiResidFull {
 // par_mode 0/1: output parity fixed, grid = ntot blocks.  par_mode 2: both
 // parities, grid = 2*ntot (block b >= ntot works on odd output sites).
 // Input is read on the opposite parity.  SPA: arithmetic-precision tag.
+// Minimum resident blocks per SM requested from the compiler.  Capping the
+// 16-bit stencils' registers for more occupancy (3 -> at most 85 registers)
+// spilled and measured slower on GB300, so every stencil asks for 1.
+#ifndef DW_HOP16_MINB
+#define DW_HOP16_MINB 1
+#endif
+template <int SPA>
+struct HopOccupancy {
+  static constexpr int kMinBlocks = (SPA == P16 || SPA == PB16) ? DW_HOP16_MINB : 1;
+};
+
 template <int SPA, int LP, bool C12, bool DAG, class In, class Epi>
-__global__ void __launch_bounds__(256) k_hop(const __grid_constant__ Batch B, int par_mode, int link_slot, In in,
-                                             Epi epi, RedArgs ra) {
+__global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
+    k_hop(const __grid_constant__ Batch B, int par_mode, int link_slot, In in, Epi epi, RedArgs ra) {
   using R = typename Spin<SPA>::R;
   DW_BLOCK_PROLOGUE(epi.gate)
   double nrm = 0.0;
@@ -483,24 +539,19 @@ __global__ void __launch_bounds__(256) k_hop(const __grid_constant__ Batch B, in
   {                                                                             \
     float eta;                                                                  \
     Cx<R> p[12], h[6], g[6], u[9];                                              \
+    R sc;                                                                       \
     const int nf = neighbour<MU, +1>(S, c, s, &eta);                            \
-    in.load(S, pin, r, nf, p);                                                  \
+    in.load_raw(S, pin, r, nf, p, sc);                                          \
     project<MU, SF>(p, h);                                                      \
     Link<LP, C12>::load(ulink_own + MU * mu_stride, S.vh, s, u);                 \
-    if (eta < 0.f) {                                                            \
-      _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im); \
-    }                                                                           \
     su3_mul<false>(u, h, g);                                                    \
-    accumulate<MU, SF>(acc, g);                                                 \
+    accumulate_w<MU, SF>(acc, g, eta < 0.f ? -sc : sc);                         \
     const int nb = neighbour<MU, -1>(S, c, s, &eta);                            \
-    in.load(S, pin, r, nb, p);                                                  \
+    in.load_raw(S, pin, r, nb, p, sc);                                          \
     project<MU, SB>(p, h);                                                      \
     Link<LP, C12>::load(ulink_nb + MU * mu_stride, S.vh, nb, u);                 \
-    if (eta < 0.f) {                                                            \
-      _Pragma("unroll") for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im); \
-    }                                                                           \
     su3_mul<true>(u, h, g);                                                     \
-    accumulate<MU, SB>(acc, g);                                                 \
+    accumulate_w<MU, SB>(acc, g, eta < 0.f ? -sc : sc);                         \
   }
     if constexpr (SPA == PDF) {
       // compact loop: one copy of the double-float mat-vec per (U, U^dag)

@@ -372,6 +372,7 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
     c.status = DW_ERR_NOT_CONVERGED;
   }
   Flags hf;
+  memset(&hf, 0, sizeof hf);
   hf.active = E.P.ncols;
   hf.rel_pending = E.P.ncols;
   hf.loops = 0;

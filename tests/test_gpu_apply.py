@@ -156,3 +156,23 @@ def test_apply_rejects_mismatches(dw):
     other = dw.spinor((4, 4, 4, 8))
     assert dw.dw_apply(Ug.handle, x.handle, other.handle, dw.current_stream()) == dw.DW_ERR_SHAPE
     assert dw.dw_apply(Ug.handle, x.handle, x.handle, dw.current_stream()) == dw.DW_ERR_ARG
+
+
+def test_pinned_host_roundtrip_is_exact(dw):
+    """Pinned host buffers are read and written directly by the layout kernels."""
+    import ctypes
+    import torch
+    dims = (8, 6, 4, 10)
+    U, psi = _setup(dims, 37)
+    hp = torch.from_numpy(psi.reshape(-1).view(np.float64).copy()).pin_memory()
+    hU = torch.from_numpy(U.reshape(-1).view(np.float64).copy()).pin_memory()
+    x = dw.spinor(dims)
+    g = dw.Field(dw.lattice(dims, 0.1), dw.DW_GAUGE)
+    dw.check(dw.dw_field_upload(x.handle, ctypes.c_void_p(hp.data_ptr()), dw.current_stream()))
+    dw.check(dw.dw_field_upload(g.handle, ctypes.c_void_p(hU.data_ptr()), dw.current_stream()))
+    out = torch.zeros_like(hp).pin_memory()
+    dw.check(dw.dw_field_download(x.handle, ctypes.c_void_p(out.data_ptr()), dw.current_stream()))
+    torch.cuda.synchronize()
+    assert np.array_equal(out.numpy().view(np.complex128).reshape(psi.shape), psi)
+    assert np.array_equal(x.download(), psi)
+    assert np.array_equal(g.download(), U)
