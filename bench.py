@@ -204,8 +204,9 @@ def run_dslash(args):
     par = (s % dims[0] + (s // dims[0]) % dims[1] + (s // (dims[0] * dims[1])) % dims[2] +
            s // (dims[0] * dims[1] * dims[2])) % 2
     Ug = dw.gauge(dims, kappa, U, prec=prec, compress12=c12)
-    x = dw.spinor(dims, b[par == 0], kind=dw.DW_SPINOR_EVEN, prec=prec)
-    y = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=prec)
+    src = b[par == 0] if args.nrhs == 1 else np.stack([np.roll(b[par == 0], r, axis=0) for r in range(args.nrhs)])
+    x = dw.spinor(dims, src, kind=dw.DW_SPINOR_EVEN, prec=prec, nrhs=args.nrhs)
+    y = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=prec, nrhs=args.nrhs)
     l2 = torch.cuda.get_device_properties(0).L2_cache_size
     scratch = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
     for _ in range(max(1, args.warmup)):
@@ -217,7 +218,8 @@ def run_dslash(args):
         dw.apply(Ug, x, y)
     prof, launches = dw.profile_stop()
     peak, kind = peaks()
-    out = {"mode": "dslash", "workload": args.workload, "prec": args.dslash, "compress12": c12, "kernels": {}}
+    out = {"mode": "dslash", "workload": args.workload, "prec": args.dslash, "compress12": c12, "nrhs": args.nrhs,
+           "kernels": {}}
     for k, e in prof.items():
         pl = e["total_ms"] / e["launches"]
         gbs = e["bytes"] / e["launches"] / (pl / 1e3) / 1e9
@@ -225,6 +227,106 @@ def run_dslash(args):
                              "bytes_per_launch": e["bytes"] / e["launches"], "gbs": gbs, "frac_hbm": gbs / peak,
                              "gflops": e["flops"] / e["launches"] / pl / 1e6}
     out["peak_gbs"] = peak
+    print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------- all workloads
+def run_suite(args):
+    """Time-to-solution of every workload configuration, mixed precision
+    against FP64, each after one warm-up solve (CUDA events, stream time)."""
+    import ctypes as C
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2001_05218_gb300 import dw
+    from paper_2001_05218_gb300 import inputs as I
+    st = torch.cuda.current_stream()
+
+    def timed(fn, reps=2):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            out = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    out = {"mode": "suite"}
+    F64 = dict(tol=1e-10, inner="f64", maxiter=100000)
+    MIX16 = dict(tol=1e-10, inner="f16", compress12=1, outer="df64", maxiter=100000)
+    MIX32 = dict(tol=1e-10, inner="f32", outer="df64", maxiter=100000)
+
+    def zero(*fields):
+        for f in fields:
+            f.storage.zero_()
+
+    def single(name, configs):
+        dims, kappa, U, b = I.make_workload(name)
+        Ug, bg, xg = dw.gauge(dims, kappa, U), dw.spinor(dims, b), dw.spinor(dims)
+        res = {}
+        for label, kw in configs:
+            p = dw.params(**kw)
+            ms, (s, stt) = timed(lambda: (zero(xg), dw.cg_solve(Ug, bg, xg, p))[1])
+            res[label] = {"ms": ms, "iters": stt[0]["iters"], "reliable_updates": stt[0]["reliable_updates"],
+                          "true_rel_resid": stt[0]["true_rel_resid"]}
+        return res
+
+    out["wilson_4x4x4x4_haar"] = single("wilson_4x4x4x4_haar", [("f64_full_lattice", dict(F64, eo=0)),
+                                                                 ("f64_eo", F64)])
+    out["wilson_16x16x16x32_exp0.4"] = single("wilson_16x16x16x32_exp0.4", [
+        ("f64", F64), ("df64", dict(tol=1e-10, inner="df64")), ("f32_mixed", MIX32), ("f16_mixed", MIX16),
+        ("f32_defect_correction", dict(MIX32, defect_correction=1))])
+    # 12 point sources on 24^3x48: one multi-RHS solve vs 12 single solves
+    name = "wilson_24x24x24x48_exp0.4_12src"
+    dims, kappa, U, _ = I.make_workload(name, with_source=False)
+    srcs = np.stack([I.point_source(dims, s_, c_) for s_ in range(4) for c_ in range(3)])
+    Ug = dw.gauge(dims, kappa, U)
+    bg, xg = dw.spinor(dims, srcs, nrhs=12), dw.spinor(dims, nrhs=12)
+    r = {}
+    for label, kw in (("f16_mixed_12rhs", MIX16), ("f64_12rhs", F64)):
+        p = dw.params(**kw)
+        ms, (s, stt) = timed(lambda: (zero(xg), dw.cg_solve(Ug, bg, xg, p))[1], reps=1)
+        r[label] = {"ms": ms, "iters_max": max(x["iters"] for x in stt),
+                    "true_rel_resid_max": max(x["true_rel_resid"] for x in stt)}
+    b1, x1 = dw.spinor(dims, srcs[0]), dw.spinor(dims)
+    p = dw.params(**MIX16)
+    ms, (s, stt) = timed(lambda: (zero(x1), dw.cg_solve(Ug, b1, x1, p))[1], reps=1)
+    r["f16_mixed_one_rhs_x12"] = {"ms": 12 * ms, "iters": stt[0]["iters"]}
+    out[name] = r
+    # ragged batch of 8 lattices: one batched solve vs the 8 solved one by one
+    systems = I.ragged_batch()
+    Us = [dw.gauge(d, k, U_) for d, k, U_, b_ in systems]
+    bs = [dw.spinor(d, b_) for d, k, U_, b_ in systems]
+    xs = [dw.spinor(d) for d, k, U_, b_ in systems]
+    r = {}
+    for label, kw in (("f16_mixed_batched", MIX16), ("f64_batched", F64)):
+        p = dw.params(**kw)
+        ms, (s, stt) = timed(lambda: (zero(*xs), dw.cg_solve_batched(Us, bs, xs, p))[1], reps=1)
+        r[label] = {"ms": ms, "iters": [x["iters"] for x in stt]}
+    p = dw.params(**MIX16)
+    ms, _ = timed(lambda: [(zero(xs[i]), dw.cg_solve(Us[i], bs[i], xs[i], p)) for i in range(len(Us))], reps=1)
+    r["f16_mixed_one_by_one"] = {"ms": ms}
+    out["ragged_batch_8"] = r
+    # differentiation: x = (D^dag D)^{-1} b forward, then grad_b and grad_U
+    dims, kappa, U, b = I.make_workload("wilson_16x16x16x32_exp0.4_grad")
+    g = I.gaussian_spinor(dims, I.workload_seed(4), I.STREAM_SOURCE2)
+    Ug, bg, gx = dw.gauge(dims, kappa, U), dw.spinor(dims, b), dw.spinor(dims, g)
+    xg, gb, gU = dw.spinor(dims), dw.spinor(dims), dw.Field(Ug.lat, dw.DW_GAUGE)
+    r = {}
+    for label, kw in (("f32_mixed", MIX32), ("f64", F64)):
+        p = dw.params(**kw)
+        sts = (dw.dw_solver_stats * 2)()
+
+        def fwd_bwd():
+            zero(xg)
+            dw.cg_solve_normal(Ug, bg, xg, p)
+            dw.check(dw.dw_cg_backward(Ug.handle, bg.handle, gx.handle, xg.handle, gb.handle, gU.handle, 1,
+                                       C.byref(p), sts, dw.current_stream()))
+        p.recompute_fwd = 0
+        ms, _ = timed(fwd_bwd, reps=1)
+        r[label] = {"ms": ms, "adjoint_iters": sts[1].iters, "adjoint_resid": sts[1].true_rel_resid}
+    out["wilson_16x16x16x32_exp0.4_grad"] = r
     print(json.dumps(out))
 
 
@@ -243,12 +345,16 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--dslash", default=None, help="stencil-only mode: f64|f32|f16|bf16 (Schur operator applies)")
+    ap.add_argument("--dslash", default=None, help="stencil-only mode: f64|f32|f16|bf16|df64 (Schur operator applies)")
+    ap.add_argument("--nrhs", type=int, default=1, help="stencil-only mode: right-hand sides per field")
+    ap.add_argument("--suite", action="store_true", help="time every workload configuration (not the benchmark line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.dslash:
         return run_dslash(args)
+    if args.suite:
+        return run_suite(args)
 
     import torch
     rank, world, local = rank_info()

@@ -185,6 +185,12 @@ typedef struct {
                           source preparation and reconstruction of a mixed solve:
                           DW_F64 (IEEE) or DW_DF64.  The final residual that
                           certifies every solve is IEEE FP64 either way. */
+  int defect_correction; /* 1: the two-data-type scheme of Strzodka & Goeddeke (the
+                          paper's Sec. 1): after every high-precision residual the
+                          low-precision CG restarts (new search direction), i.e.
+                          outer defect correction with inner solves to relative
+                          accuracy delta.  0: reliable updates (the search
+                          direction is kept across corrections). */
 } dw_solver_params;
 
 typedef struct {
@@ -200,7 +206,7 @@ typedef struct {
 
 /* Fill *p with defaults: tol 1e-10, maxiter 20000, inner DW_F32, delta 0.1,
  * eo 1, compress12 0, recompute_fwd 1, tile 0, check_every 0, timeout 0,
- * verify_normal 0, outer DW_F64.
+ * verify_normal 0, outer DW_F64, defect_correction 0.
  * The CG loop runs as one CUDA graph: a device-side while-loop over the
  * iteration, with the FP64 reliable update in a conditional node; the host
  * waits once per solve.  While dw_profile_start is active the loop is stepped

@@ -574,11 +574,12 @@ struct ColState {
   double store[4]; // scalar outputs of plain reductions
   unsigned long long deadline_ns;  // globaltimer deadline (0 = none)
   int iter, maxiter, nrel;
+  int defect;      // 1: restart the low-precision CG after every high-precision correction
   int active;      // 1 while iterating
   int do_rel;      // reliable update pending
   int status;      // dw_status of this column
   int xzero;       // initial guess is zero: the first residual is the source itself
-  int pad;
+  int restart;     // defect correction: the next beta is 0 (new search direction)
 };
 
 // Batch-wide flags.
@@ -681,6 +682,7 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
       C.rr = v;
       C.rr_ref = v;
       C.nrel += 1;
+      if (C.defect) C.restart = 1;
       bool timeout = C.deadline_ns != 0ull && globaltimer_ns() > C.deadline_ns;
       if (v <= C.tol2) deactivate(C, ra.flags, 0);
       else if (!isfinite(v)) deactivate(C, ra.flags, 7);
@@ -695,7 +697,8 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
       break;
     case FIN_BETA:
       if (!C.active) break;
-      C.beta = v / C.gamma;
+      C.beta = C.restart ? 0.0 : v / C.gamma;
+      C.restart = 0;
       C.gamma = v;
       break;
   }

@@ -506,15 +506,20 @@ struct EpiResidFull {
 // par_mode 0/1: output parity fixed, grid = ntot blocks.  par_mode 2: both
 // parities, grid = 2*ntot (block b >= ntot works on odd output sites).
 // Input is read on the opposite parity.  SPA: arithmetic-precision tag.
-// Minimum resident blocks per SM requested from the compiler.  Capping the
-// 16-bit stencils' registers for more occupancy (3 -> at most 85 registers)
-// spilled and measured slower on GB300, so every stencil asks for 1.
+// Minimum resident blocks (of 256 threads) per SM requested from the compiler.
+// Measured on GB300: capping the double-float stencil at 128 registers (2)
+// runs 9% faster despite small spills (more warps to hide its long dependency
+// chains); capping the 16-bit stencils at 85 registers (3) spilled and ran
+// slower, so they ask for 1.
 #ifndef DW_HOP16_MINB
 #define DW_HOP16_MINB 1
 #endif
+#ifndef DW_HOPDF_MINB
+#define DW_HOPDF_MINB 2
+#endif
 template <int SPA>
 struct HopOccupancy {
-  static constexpr int kMinBlocks = (SPA == P16 || SPA == PB16) ? DW_HOP16_MINB : 1;
+  static constexpr int kMinBlocks = (SPA == P16 || SPA == PB16) ? DW_HOP16_MINB : SPA == PDF ? DW_HOPDF_MINB : 1;
 };
 
 template <int SPA, int LP, bool C12, bool DAG, class In, class Epi>

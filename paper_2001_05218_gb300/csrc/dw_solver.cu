@@ -110,6 +110,7 @@ dw_status dw_solver_params_default(dw_solver_params* p) {
   p->timeout_s = 0;
   p->verify_normal = 0;
   p->outer = DW_F64;
+  p->defect_correction = 0;
   return DW_OK;
 }
 

@@ -367,6 +367,7 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
     c.tol2 = a.p.tol * a.p.tol;
     c.delta2 = (L == P64 || L == PDF) ? 0.0 : a.p.delta * a.p.delta;
     c.maxiter = a.p.maxiter;
+    c.defect = a.p.defect_correction ? 1 : 0;
     c.active = 1;
     c.do_rel = 1;  // the first FP64 residual is a "reliable update" unless x0 = 0
     c.status = DW_ERR_NOT_CONVERGED;

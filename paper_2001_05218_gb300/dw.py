@@ -41,7 +41,8 @@ class dw_solver_params(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxiter", ctypes.c_int), ("inner", ctypes.c_int),
                 ("delta", ctypes.c_double), ("eo", ctypes.c_int), ("compress12", ctypes.c_int),
                 ("recompute_fwd", ctypes.c_int), ("tile", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("timeout_s", ctypes.c_double), ("verify_normal", ctypes.c_int), ("outer", ctypes.c_int)]
+                ("timeout_s", ctypes.c_double), ("verify_normal", ctypes.c_int), ("outer", ctypes.c_int),
+                ("defect_correction", ctypes.c_int)]
 
 
 class dw_profile_entry(ctypes.Structure):

@@ -146,3 +146,19 @@ def test_not_converged_and_bad_source(dw):
     s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-14, inner="f32", timeout_s=1e-9, maxiter=100000),
                         raise_on_fail=False)
     assert s == dw.DW_ERR_TIMEOUT
+
+
+@pytest.mark.parametrize("inner,delta", [("f32", 0.1), ("f16", 0.1), ("f32", 1e-3)])
+def test_defect_correction_solves(dw, inner, delta):
+    """The paper's two-data-type scheme: restarted low-precision inner CG,
+    high-precision outer residual; reaches the same FP64 bound."""
+    dims, kappa = (8, 8, 8, 16), 0.123
+    U = I.gauge_field(dims, "exp", 12, 1, 0.4)
+    b = I.gaussian_spinor(dims, 12, 2)
+    Ug = dw.gauge(dims, kappa, U)
+    bg = dw.spinor(dims, b)
+    x = dw.spinor(dims)
+    s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner=inner, delta=delta, defect_correction=1,
+                                             outer="df64", compress12=1 if inner == "f16" else 0))
+    assert s == dw.DW_OK and st[0]["reliable_updates"] >= 1
+    assert _resid(dims, kappa, U, x.download(), b) <= 1e-10
