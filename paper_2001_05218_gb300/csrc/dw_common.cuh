@@ -740,6 +740,19 @@ __device__ __forceinline__ void reduce_finalize(const SysDesc& S, int T, int RB,
   __syncthreads();
   if (!am_last) return;
   __threadfence();
+  const int nw = (int)(blockDim.x >> 5);
+  if (S.nrhs >= nw) {
+    // one warp per column, columns assigned round-robin (fixed order)
+    for (int r = warp; r < S.nrhs; r += nw) {
+      double s = 0.0;
+      for (int i = lane; i < ntiles; i += 32) s += __ldcg(ra.partial + S.part0 + r * ntiles + i);
+      s = warp_sum(s);
+      if (lane == 0) finalize(ra, S.col0 + r, s);
+    }
+    __syncthreads();
+    if (tid == 0) ra.counter[S.sys] = 0;
+    return;
+  }
   for (int r = 0; r < S.nrhs; ++r) {
     double s = 0.0;
     for (int i = tid; i < ntiles; i += blockDim.x) s += __ldcg(ra.partial + S.part0 + r * ntiles + i);
