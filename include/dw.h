@@ -217,8 +217,9 @@ dw_status dw_solver_params_default(dw_solver_params* p);
 /* Solve D x = b by CG on the normal equations D^dag D x = D^dag b (with the
  * even-odd Schur system when p->eo).  U: FP64 gauge field (18 reals).  b, x:
  * FP64 FULL spinors of equal nrhs; every right-hand side is solved.  x holds
- * the initial guess on entry.  stats: one entry per right-hand side (may be
- * NULL).  Returns the worst status over right-hand sides. */
+ * the initial guess on entry; a right-hand side with b = 0 returns x = 0.
+ * stats: one entry per right-hand side (may be NULL).  Returns the worst
+ * status over right-hand sides. */
 dw_status dw_cg_solve(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
                       dw_solver_stats* stats, dw_stream_t stream);
 

@@ -580,6 +580,8 @@ struct ColState {
   int status;      // dw_status of this column
   int xzero;       // initial guess is zero: the first residual is the source itself
   int restart;     // defect correction: the next beta is 0 (new search direction)
+  int zsrc;        // zero source: the solution is x = 0
+  int pad;
 };
 
 // Batch-wide flags.
@@ -637,7 +639,14 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
     case FIN_STORE1: C.store[1] = v; break;
     case FIN_STORE2: C.store[2] = v; break;
     case FIN_STORE3: C.store[3] = v; break;
-    case FIN_BNORM: C.bnorm2 = v; C.tol2 = C.tol2 * v; break;
+    case FIN_BNORM:
+      C.bnorm2 = v;
+      C.tol2 = C.tol2 * v;
+      if (v == 0.0) {  // D x = 0 has the solution x = 0: nothing to iterate
+        C.zsrc = 1;
+        deactivate(C, ra.flags, 0);
+      }
+      break;
     case FIN_ALPHA:
       if (!C.active) break;
       if (!(v > 0.0) || !isfinite(v) || !isfinite(C.gamma)) {

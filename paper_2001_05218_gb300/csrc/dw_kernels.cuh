@@ -23,7 +23,7 @@
 namespace dw {
 
 enum Coef { C_ONE = 0, C_MK, C_PK, C_MK2, C_PK2 };
-enum Gate { G_ACTIVE = 0, G_REL, G_ALL, G_XZERO };
+enum Gate { G_ACTIVE = 0, G_REL, G_ALL, G_XZERO, G_ZSRC };
 
 template <int C>
 __device__ __forceinline__ double coef_of(double kappa) {
@@ -33,6 +33,7 @@ __device__ __forceinline__ double coef_of(double kappa) {
 __device__ __forceinline__ int gate_of(int g, const ColState* cols, int col) {
   if (g == G_ALL) return 1;
   if (g == G_XZERO) return cols[col].xzero;
+  if (g == G_ZSRC) return cols[col].zsrc;
   return g == G_ACTIVE ? cols[col].active : cols[col].do_rel;
 }
 
@@ -703,6 +704,18 @@ __global__ void __launch_bounds__(256) k_norm(const __grid_constant__ Batch B, i
     for (int k = 0; k < 12; ++k) nrm = fma((double)v[k].re, (double)v[k].re, fma((double)v[k].im, (double)v[k].im, nrm));
   }
   DW_BLOCK_REDUCE(nrm)
+}
+
+// field <- 0 for the columns with a zero source (gate G_ZSRC)
+template <int SP>
+__global__ void __launch_bounds__(256) k_zero_zsrc(const __grid_constant__ Batch B, int par_mode, int slot, RedArgs ra) {
+  DW_BLOCK_PROLOGUE(G_ZSRC)
+  if (valid) {
+    Cx<typename Spin<SP>::R> z[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) z[k] = cx((typename Spin<SP>::R)0, (typename Spin<SP>::R)0);
+    Spin<SP>::store(slot_wptr(S, slot, r, par), S.vh, s, z);
+  }
 }
 
 // dst = convert(src), over the launched parities (gate: all)

@@ -441,6 +441,8 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
     count_launch();
     k_convert<P64, H><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_XU, S_X, E.ra(FIN_STORE0));
   }
+  count_launch();
+  k_zero_zsrc<P64><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_XU, E.ra(FIN_STORE0));  // zero source: x = 0
   const int rt64 = H == P64 ? S_RT : S_AUX1;  // FP64 full temporary (verify_normal)
   if (mode != MODE_NORMAL) {
     hop<P64, P64, false, false>(E, 2, S_LF64, InOne<P64>{S_XU},
