@@ -43,6 +43,28 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def aggregate_throughput(local_ms, steps, world, device):
+    """Whole-job throughput: every rank solved `steps` systems in its own
+    timed region; the job's time is the slowest rank's (MAX all-reduce, the
+    only collective, outside the timed region).  Returns (solves/s, max ms)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    return world * steps / (total_ms / 1e3), total_ms
+
+
+def rank_source_seed(workload, rank):
+    """Seed of the source solved by `rank`: rank 0 solves the workload's own
+    system, every other rank an independent seeded source on the same links."""
+    from paper_2001_05218_gb300 import inputs as I
+    base = I.workload_seed(I.WORKLOADS[workload]["index"])
+    return base if rank == 0 else base + 1000 * rank
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -378,7 +400,7 @@ def main():
     c12 = args.compress12 if args.compress12 is not None else (1 if inner in ("f16", "bf16") else 0)
     dims, kappa, U, b = I.make_workload(wl)
     if rank > 0:  # independent system per rank: a different seeded source
-        b = I.gaussian_spinor(dims, I.workload_seed(I.WORKLOADS[wl]["index"]) + 1000 * rank, I.STREAM_SOURCE)
+        b = I.gaussian_spinor(dims, rank_source_seed(wl, rank), I.STREAM_SOURCE)
     V = int(np.prod(dims))
     Ug = dw.gauge(dims, kappa, U)
     bg = dw.spinor(dims, b)
@@ -426,14 +448,9 @@ def main():
     barrier()
     _, launches = dw.profile_stop()
     clocks = clk.stop()
-    total_ms = t0.elapsed_time(t1)
     step_ms = [a.elapsed_time(b_) for a, b_ in ev]
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    value, total_ms = aggregate_throughput(t0.elapsed_time(t1), args.steps, world, "cuda")
     solve_ms = float(np.mean(step_ms))
-    value = world * args.steps / (total_ms / 1e3)
     st0 = stats[-1]
 
     # per-launch stencil times: one more solve of the same system, stepped from

@@ -32,16 +32,59 @@ enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PDF = 4 };
 // transforms are Knuth's TwoSum, Dekker's Fast2Sum and the FMA form of
 // TwoProduct; every step uses explicitly rounded intrinsics so the compiler
 // cannot contract or reorder them.
+// Conversions between binary64 and the (hi, lo) pair use integer bit
+// operations (GB300's FP64 pipe runs at 1/61 of the FP32 rate):
+//   d -> hi = sign | exponent | top 23 mantissa bits of d (truncated),
+//        lo = the low 29 mantissa bits scaled by 2^(e - 1075), rounded to 24
+//        bits: |d - (hi + lo)| <= 2^-47 |d|.  Values below 2^-126 flush to 0,
+//        lo flushes below 2^-74; infinities and NaN keep their class.
+//   (hi, lo) -> d = widen(hi) + widen(lo) with exact bit widening and one
+//        FP64 add.
+__device__ __forceinline__ void split_double(double d, float& h, float& l) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned hw = (unsigned)(b >> 32), lw = (unsigned)b;
+  const unsigned sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu);
+  const int ef = e - 896;  // float biased exponent
+  const unsigned mant23 = ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+  if (e == 0x7FF) {
+    h = __uint_as_float(sign | 0x7F800000u | (((hw & 0xFFFFFu) | lw) ? 0x400000u : 0u));
+    l = 0.f;
+    return;
+  }
+  if (ef <= 0) {
+    h = __uint_as_float(sign);
+    l = 0.f;
+    return;
+  }
+  if (ef >= 255) {
+    h = __uint_as_float(sign | 0x7F800000u);
+    l = 0.f;
+    return;
+  }
+  h = __uint_as_float(sign | ((unsigned)ef << 23) | mant23);
+  const int es = e - 948;  // biased float exponent of 2^(e - 1075)
+  const float r = __uint2float_rn(lw & 0x1FFFFFFFu);
+  const float lm = es > 0 ? __fmul_rn(r, __uint_as_float((unsigned)es << 23)) : 0.f;
+  l = sign ? -lm : lm;
+}
+__device__ __forceinline__ double widen_float(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  const unsigned e = (b >> 23) & 0xFFu;
+  const unsigned long long m = (unsigned long long)(b & 0x7FFFFFu) << 29;
+  if (e == 0u) return __longlong_as_double((long long)sign);  // zero (FP32 denormals flush)
+  const unsigned long long de = e == 0xFFu ? 0x7FFull : (unsigned long long)(e + 896u);
+  return __longlong_as_double((long long)(sign | (de << 52) | m));
+}
+
 struct DF {
   float hi, lo;
   DF() = default;
   __host__ __device__ explicit DF(int v) : hi((float)v), lo(0.f) {}
   __host__ __device__ explicit DF(float v) : hi(v), lo(0.f) {}
-  __device__ explicit DF(double d) {
-    hi = __double2float_rn(d);
-    lo = __double2float_rn(d - (double)hi);
-  }
-  __device__ explicit operator double() const { return (double)hi + (double)lo; }
+  __device__ explicit DF(double d) { split_double(d, hi, lo); }
+  __device__ explicit operator double() const { return widen_float(hi) + widen_float(lo); }
   __device__ explicit operator float() const { return hi + lo; }
 };
 
