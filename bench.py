@@ -362,7 +362,7 @@ def main():
     ap.add_argument("--inner", default=None)
     ap.add_argument("--compress12", type=int, default=None)
     ap.add_argument("--outer", default="df64", help="precision of the reliable updates: df64 or f64")
-    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold")
+    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (default: automatic)")
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -569,7 +569,8 @@ def main():
         if inner not in ("f64", "df64") else inner,
         "data": "synthetic (seeded exp(i a H) links, Gaussian source)",
         "config": {"workload": wl, "lattice": list(dims), "kappa": kappa, "solver": "even-odd CGNR",
-                   "inner": inner, "compress12": c12, "outer": args.outer, "delta": p_mix.delta,
+                   "inner": inner, "compress12": c12, "outer": args.outer,
+                   "delta": p_mix.delta if p_mix.delta > 0 else ("auto: 0.03" if inner in ("f16", "bf16") else "auto: 1e-3"),
                    "certification": "IEEE FP64",
                    "tol": 1e-10, "global_batch": world, "parallelism": "replicas",
                    "l2": "flushed between steps" if flush else "inputs larger than L2 (%d MB working set)" %

@@ -171,7 +171,10 @@ typedef struct {
   dw_prec inner;       /* DW_F64: plain FP64 CG.  DW_DF64: plain CG in double-float.
                           DW_F32/F16/BF16: mixed-precision CG with reliable updates
                           in the `outer` precision */
-  double delta;        /* reliable update when |r| < delta * |r at last update| */
+  double delta;        /* reliable update when |r| < delta * |r at last update|;
+                          0 = by inner precision: 0.03 for FP16/BF16 storage, 1e-3
+                          for FP32 (the low-precision recursion drifts by about
+                          unit roundoff / delta between corrections) */
   int eo;              /* 1: even-odd preconditioned (Schur system on even sites) */
   int compress12;      /* inner-precision links stored as 12 reals */
   int recompute_fwd;   /* dw_cg_backward: 1 = recompute the forward solution */
@@ -204,7 +207,7 @@ typedef struct {
   int status;             /* dw_status of this system */
 } dw_solver_stats;
 
-/* Fill *p with defaults: tol 1e-10, maxiter 20000, inner DW_F32, delta 0.1,
+/* Fill *p with defaults: tol 1e-10, maxiter 20000, inner DW_F32, delta 0 (automatic),
  * eo 1, compress12 0, recompute_fwd 1, tile 0, check_every 0, timeout 0,
  * verify_normal 0, outer DW_F64, defect_correction 0.
  * The CG loop runs as one CUDA graph: a device-side while-loop over the

@@ -133,25 +133,37 @@ __device__ __forceinline__ DF fma(DF a, DF b, DF c) {
   return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(c.lo, e)));
 }
 
-// Sum of n products x_i * y_i: exact high products chained with TwoSum, all
-// low-order terms collected in one FP32 accumulator, one renormalisation.
-template <int N>
-__device__ __forceinline__ DF df_dot(const DF (&x)[N], const DF (&y)[N]) {
-  float S = __fmul_rn(x[0].hi, y[0].hi);
-  float E = __fmaf_rn(x[0].hi, y[0].hi, -S);
-  E = __fmaf_rn(x[0].hi, y[0].lo, E);
-  E = __fmaf_rn(x[0].lo, y[0].hi, E);
-#pragma unroll
-  for (int i = 1; i < N; ++i) {
-    const float p = __fmul_rn(x[i].hi, y[i].hi);
-    E = __fadd_rn(E, __fmaf_rn(x[i].hi, y[i].hi, -p));
-    E = __fmaf_rn(x[i].hi, y[i].lo, E);
-    E = __fmaf_rn(x[i].lo, y[i].hi, E);
-    const DF t = two_sum(S, p);
-    S = t.hi;
-    E = __fadd_rn(E, t.lo);
-  }
-  return fast_two_sum(S, E);
+// Sum with the hi parts added exactly and everything else collected in lo,
+// without renormalising: for values that feed further double-float
+// operations, which accept any (hi, lo) with |lo| << |hi|.
+__device__ __forceinline__ DF add_lazy(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return df_make(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ DF renorm(DF a) { return fast_two_sum(a.hi, a.lo); }
+
+// Exact high product and its low-order terms: x*y = p + e (+ x.lo*y.lo).
+__device__ __forceinline__ DF prod_terms(DF x, DF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return df_make(p, e);
+}
+
+// Sum of 6 products x_i * y_i: exact high products added pairwise with TwoSum
+// (a tree, so the three first-level sums are independent), all low-order
+// terms collected in FP32, one renormalisation.
+__device__ __forceinline__ DF df_dot6(const DF (&x)[6], const DF (&y)[6]) {
+  const DF a = prod_terms(x[0], y[0]), b = prod_terms(x[1], y[1]), c = prod_terms(x[2], y[2]);
+  const DF d = prod_terms(x[3], y[3]), e = prod_terms(x[4], y[4]), f = prod_terms(x[5], y[5]);
+  const DF ab = two_sum(a.hi, b.hi), cd = two_sum(c.hi, d.hi), ef = two_sum(e.hi, f.hi);
+  const DF abcd = two_sum(ab.hi, cd.hi);
+  const DF all = two_sum(abcd.hi, ef.hi);
+  const float lo1 = __fadd_rn(__fadd_rn(a.lo, b.lo), __fadd_rn(c.lo, d.lo));
+  const float lo2 = __fadd_rn(__fadd_rn(e.lo, f.lo), __fadd_rn(ab.lo, cd.lo));
+  const float lo3 = __fadd_rn(__fadd_rn(ef.lo, abcd.lo), all.lo);
+  return fast_two_sum(all.hi, __fadd_rn(__fadd_rn(lo1, lo2), lo3));
 }
 
 

@@ -155,8 +155,8 @@ __device__ __forceinline__ void su3_mul(const Cx<DF> (&u)[9], const Cx<DF> (&h)[
         xi[2 * b + 1] = ADJ ? -m.im : m.im;
         yi[2 * b + 1] = v.re;
       }
-      g[3 * k + a].re = df_dot(xr, yr);
-      g[3 * k + a].im = df_dot(xi, yi);
+      g[3 * k + a].re = df_dot6(xr, yr);
+      g[3 * k + a].im = df_dot6(xi, yi);
     }
 }
 
@@ -194,26 +194,29 @@ __device__ __forceinline__ DirSpin dir_spin(int mu, int s) {
   d.d3 = UnitFactor{im, (mu == 1 || mu == 2) ? !neg_s : neg_s};
   return d;
 }
+// complex sums for the double-float path: lazy (no renormalisation)
+__device__ __forceinline__ Cx<DF> cadd_lazy(Cx<DF> a, Cx<DF> b) { return cx(add_lazy(a.re, b.re), add_lazy(a.im, b.im)); }
 template <typename R>
 __device__ __forceinline__ void project_rt(const DirSpin& d, const Cx<R> (&p)[12], Cx<R> (&h)[6]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const Cx<R> q0 = d.swap ? p[9 + c] : p[6 + c];
     const Cx<R> q1 = d.swap ? p[6 + c] : p[9 + c];
-    h[c] = p[c] + mul_unit(q0, d.c0);
-    h[3 + c] = p[3 + c] + mul_unit(q1, d.c1);
+    h[c] = cadd_lazy(p[c], mul_unit(q0, d.c0));
+    h[3 + c] = cadd_lazy(p[3 + c], mul_unit(q1, d.c1));
   }
 }
+// acc stays unnormalised across the eight directions (renormalised by the caller)
 template <typename R>
 __device__ __forceinline__ void accumulate_rt(const DirSpin& d, Cx<R> (&acc)[12], const Cx<R> (&g)[6]) {
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    acc[c] = acc[c] + g[c];
-    acc[3 + c] = acc[3 + c] + g[3 + c];
+    acc[c] = cadd_lazy(acc[c], g[c]);
+    acc[3 + c] = cadd_lazy(acc[3 + c], g[3 + c]);
     const Cx<R> g2 = d.swap ? g[3 + c] : g[c];
     const Cx<R> g3 = d.swap ? g[c] : g[3 + c];
-    acc[6 + c] = acc[6 + c] + mul_unit(g2, d.d2);
-    acc[9 + c] = acc[9 + c] + mul_unit(g3, d.d3);
+    acc[6 + c] = cadd_lazy(acc[6 + c], mul_unit(g2, d.d2));
+    acc[9 + c] = cadd_lazy(acc[9 + c], mul_unit(g3, d.d3));
   }
 }
 
@@ -587,6 +590,8 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
         su3_mul<true>(u, h, g);
         accumulate_rt(db, acc, g);
       }
+#pragma unroll
+      for (int k = 0; k < 12; ++k) acc[k] = cx(renorm(acc[k].re), renorm(acc[k].im));
     } else {
       DW_HOP_DIR(0)
       DW_HOP_DIR(1)

@@ -44,8 +44,8 @@ static dw_status check_params(const dw_solver_params* p) {
   DW_CHECK(p->maxiter > 0, DW_ERR_ARG, "maxiter must be positive");
   DW_CHECK(p->inner >= DW_F64 && p->inner <= DW_DF64, DW_ERR_PRECISION, "unknown inner precision");
   DW_CHECK(p->outer == DW_F64 || p->outer == DW_DF64, DW_ERR_PRECISION, "outer precision must be DW_F64 or DW_DF64");
-  DW_CHECK(p->inner == DW_F64 || p->inner == DW_DF64 || (p->delta > 0 && p->delta < 1), DW_ERR_ARG,
-           "delta %g must lie in (0, 1)",
+  DW_CHECK(p->inner == DW_F64 || p->inner == DW_DF64 || (p->delta >= 0 && p->delta < 1), DW_ERR_ARG,
+           "delta %g must lie in [0, 1) (0: chosen by inner precision)",
            p->delta);
   DW_CHECK(p->tile == 0 || (p->tile >= 32 && p->tile <= 256 && p->tile % 32 == 0), DW_ERR_ARG,
            "tile %d must be 0 or a multiple of 32 in [32, 256]", p->tile);
@@ -79,6 +79,8 @@ dw_status solve_many(int n, const dw_field* const* U, const dw_field* const* b, 
     a.b = b + g;
     a.x = x + g;
     a.p = *p;
+    if (a.p.delta <= 0.0)  // reliable-update threshold by inner precision
+      a.p.delta = (a.p.inner == DW_F16 || a.p.inner == DW_BF16) ? 0.03 : 1e-3;
     if (mode == MODE_EO && !p->eo) mode = MODE_FULL;
     a.mode = mode;
     a.stats = stats ? stats + (size_t)g * nrhs : nullptr;
@@ -101,7 +103,7 @@ dw_status dw_solver_params_default(dw_solver_params* p) {
   p->tol = 1e-10;
   p->maxiter = 20000;
   p->inner = DW_F32;
-  p->delta = 0.1;
+  p->delta = 0.0;  // automatic: 0.03 for 16-bit inner storage, 1e-3 for FP32
   p->eo = 1;
   p->compress12 = 0;
   p->recompute_fwd = 1;

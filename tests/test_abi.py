@@ -51,7 +51,7 @@ def test_field_bytes_and_shape_checks(dw):
 
 def test_params_default_and_null_checks(dw):
     p = dw.params()
-    assert abs(p.tol - 1e-10) < 1e-25 and p.inner == dw.DW_F32 and p.eo == 1 and abs(p.delta - 0.1) < 1e-15
+    assert abs(p.tol - 1e-10) < 1e-25 and p.inner == dw.DW_F32 and p.eo == 1 and p.delta == 0.0
     assert dw.dw_apply(None, None, None, None) == dw.DW_ERR_ARG
     assert dw.dw_cg_solve(None, None, None, ctypes.byref(p), None, None) == dw.DW_ERR_ARG
     assert dw.dw_field_free(None) == dw.DW_OK
