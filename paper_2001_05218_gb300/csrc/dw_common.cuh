@@ -592,7 +592,9 @@ struct SysDesc {
   int tpp;              // thread blocks per parity for this system
   int tile0;            // first block (within one parity) of this system
   int col0;             // first column (system, rhs) index
-  int part0;            // first partial-sum slot
+  int part0;            // first partial-sum slot (one per block and column)
+  int part2_0;          // first group-sum slot (one per group of kRedGroup blocks and column)
+  int cnt0;             // first arrival counter: [cnt0] groups done, [cnt0 + 1 + g] blocks of group g
   int sys;              // system index
   double kappa;
   Slot f[kNumSlots];
@@ -774,13 +776,56 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// A block holds RB groups of T threads (T a multiple of 32); group g works
-// on right-hand side r = blockIdx.y*RB + g.  Each group's values are summed in
-// a fixed order and written as this block's partial; the last block of the
-// system to arrive (per-system arrival counter, ntiles*gridDim.y arrivals)
-// sums every column's partials in a fixed order and runs the finalizer, so
-// results are bitwise reproducible run to run.  Every thread of the block
-// must call this.
+// Two-level deterministic grid reduction.  A block holds RB groups of T
+// threads (T a multiple of 32); group g works on right-hand side
+// r = blockIdx.y*RB + g.  Each group's values are summed in a fixed order and
+// written as the block's partial.  Blocks are grouped by tile, kRedGroup tiles
+// per group: the last block of a group to arrive (per-group arrival counter)
+// sums the group's partials of every column in a fixed order, and the last
+// group to finish sums the group sums and runs the finalizer.  Each level
+// reads at most kRedGroup values per column, so the serial tail stays short,
+// and every sum has a fixed order, so results are bitwise reproducible.
+// Every thread of the block must call this.
+constexpr int kRedGroup = 128;
+
+// Sum of n values (n <= kRedGroup * 2) of one column in a fixed order by the
+// threads of one warp (lane-strided, then a fixed butterfly).
+__device__ __forceinline__ double warp_sum_column(const double* p, int n, int lane) {
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += __ldcg(p + i);
+  return warp_sum(s);
+}
+
+// Sum over columns of the values p[r * stride + i], i < n, r < ncol; result
+// per column goes to fn(r, sum), called by one thread.  Fixed order.
+template <class Fn>
+__device__ __forceinline__ void sum_columns(const double* p, int stride, int n, int ncol, Fn fn, double* wsum) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nw = (int)(blockDim.x >> 5);
+  if (ncol >= nw) {
+    for (int r = warp; r < ncol; r += nw) {
+      const double s = warp_sum_column(p + r * stride, n, lane);
+      if (lane == 0) fn(r, s);
+    }
+    __syncthreads();
+    return;
+  }
+  for (int r = 0; r < ncol; ++r) {
+    double s = 0.0;
+    for (int i = tid; i < n; i += blockDim.x) s += __ldcg(p + r * stride + i);
+    s = warp_sum(s);
+    __syncthreads();
+    if (lane == 0) wsum[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double t = 0.0;
+      for (int w = 0; w < nw; ++w) t += wsum[w];
+      fn(r, t);
+    }
+  }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void reduce_finalize(const SysDesc& S, int T, int RB, int tile, int ntiles, double v,
                                                 const RedArgs& ra) {
   __shared__ double wsum[32];
@@ -800,37 +845,30 @@ __device__ __forceinline__ void reduce_finalize(const SysDesc& S, int T, int RB,
   }
   __threadfence();
   __syncthreads();
-  if (tid == 0) am_last = (atomicAdd(&ra.counter[S.sys], 1) == ntiles * (int)gridDim.y - 1);
+  const int g = tile / kRedGroup;
+  const int ngroups = (ntiles + kRedGroup - 1) / kRedGroup;
+  const int g0 = g * kRedGroup;
+  const int gsize = ntiles - g0 < kRedGroup ? ntiles - g0 : kRedGroup;
+  if (tid == 0) am_last = (atomicAdd(&ra.counter[S.cnt0 + 1 + g], 1) == gsize * (int)gridDim.y - 1);
   __syncthreads();
   if (!am_last) return;
   __threadfence();
-  const int nw = (int)(blockDim.x >> 5);
-  if (S.nrhs >= nw) {
-    // one warp per column, columns assigned round-robin (fixed order)
-    for (int r = warp; r < S.nrhs; r += nw) {
-      double s = 0.0;
-      for (int i = lane; i < ntiles; i += 32) s += __ldcg(ra.partial + S.part0 + r * ntiles + i);
-      s = warp_sum(s);
-      if (lane == 0) finalize(ra, S.col0 + r, s);
-    }
-    __syncthreads();
-    if (tid == 0) ra.counter[S.sys] = 0;
-    return;
+  // level 1: this group's partials -> one group sum per column
+  double* part2 = ra.partial + S.part2_0;
+  sum_columns(ra.partial + S.part0 + g0, ntiles, gsize, S.nrhs,
+              [&](int r, double sum) { part2[r * ngroups + g] = sum; }, wsum);
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    ra.counter[S.cnt0 + 1 + g] = 0;
+    am_last = (atomicAdd(&ra.counter[S.cnt0], 1) == ngroups - 1);
   }
-  for (int r = 0; r < S.nrhs; ++r) {
-    double s = 0.0;
-    for (int i = tid; i < ntiles; i += blockDim.x) s += __ldcg(ra.partial + S.part0 + r * ntiles + i);
-    s = warp_sum(s);
-    __syncthreads();
-    if (lane == 0) wsum[warp] = s;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wsum[w];
-      finalize(ra, S.col0 + r, t);
-    }
-  }
-  if (tid == 0) ra.counter[S.sys] = 0;
+  __syncthreads();
+  if (!am_last) return;
+  __threadfence();
+  // level 2: group sums -> column totals -> finalizer
+  sum_columns(part2, ngroups, ngroups, S.nrhs, [&](int r, double sum) { finalize(ra, S.col0 + r, sum); }, wsum);
+  if (tid == 0) ra.counter[S.cnt0] = 0;
 }
 
 // Cooperative copy of this block's system descriptor into shared memory.

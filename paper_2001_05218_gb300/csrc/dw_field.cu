@@ -129,7 +129,7 @@ void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T, in
   P.B.nsys = P.nsys;
   P.B.T = T;
   P.B.RB = RB;
-  int tile = 0, part = 0;
+  int tile = 0, part = 0, cnt = 0;
   for (int i = 0; i < P.nsys; ++i) {
     SysDesc& S = P.B.sd[i];
     geometry(S, lats[i], nrhs);
@@ -139,11 +139,17 @@ void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T, in
     S.part0 = part;
     S.sys = i;
     tile += S.tpp;
-    part += nrhs * 2 * S.tpp;
+    part += nrhs * 2 * S.tpp;  // block partials (both-parity launches hold 2*tpp tiles)
+    const int ngroups = (2 * S.tpp + kRedGroup - 1) / kRedGroup;
+    S.part2_0 = part;
+    part += nrhs * ngroups;    // group sums
+    S.cnt0 = cnt;
+    cnt += 1 + ngroups;        // arrival counters
   }
   P.B.ntot = tile;
   P.ncols = P.nsys * nrhs;
   P.partials = part;
+  P.counters = cnt;
   const int gy = (nrhs + RB - 1) / RB;
   P.block = dim3(T * RB);
   P.grid1 = dim3(tile, gy);

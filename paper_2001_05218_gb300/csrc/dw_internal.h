@@ -76,7 +76,8 @@ void geometry(SysDesc& S, const dw_lattice& l, int nrhs);
 struct Plan {
   Batch B;
   int nsys = 0, nrhs = 1, ncols = 0;
-  int partials = 0;  // doubles in the partial-sum buffer
+  int partials = 0;  // doubles in the partial-sum buffer (block partials and group sums)
+  int counters = 0;  // ints of arrival counters
   dim3 block, grid1, grid2;  // one parity / both parities
 };
 // T sites per block and RB right-hand sides per block (T*RB <= 256, T a

@@ -323,14 +323,14 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
         total += al((size_t)nrhs * pc.npar * spin_bytes(pc.prec) * vh);
       }
     }
-    const size_t red_bytes = al(sizeof(double) * F.P.partials) + al(sizeof(int) * kMaxSys) +
+    const size_t red_bytes = al(sizeof(double) * F.P.partials) + al(sizeof(int) * F.P.counters) +
                              al(sizeof(ColState) * F.P.ncols) + al(sizeof(Flags));
     DW_CUDA(cudaMalloc((void**)&fresh.arena, total + red_bytes));
     char* rp = fresh.arena + total;
     F.rb.partial = reinterpret_cast<double*>(rp);
     rp += al(sizeof(double) * F.P.partials);
     F.rb.counter = reinterpret_cast<int*>(rp);
-    rp += al(sizeof(int) * kMaxSys);
+    rp += al(sizeof(int) * F.P.counters);
     F.rb.cols = reinterpret_cast<ColState*>(rp);
     rp += al(sizeof(ColState) * F.P.ncols);
     F.rb.flags = reinterpret_cast<Flags*>(rp);
@@ -384,7 +384,7 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
   DW_CUDA(cudaEventRecord(ev0, st));
   DW_CUDA(cudaMemcpyAsync(E.rb.cols, hc.data(), sizeof(ColState) * hc.size(), cudaMemcpyHostToDevice, st));
   DW_CUDA(cudaMemcpyAsync(E.rb.flags, &hf, sizeof hf, cudaMemcpyHostToDevice, st));
-  DW_CUDA(cudaMemsetAsync(E.rb.counter, 0, sizeof(int) * kMaxSys, st));
+  DW_CUDA(cudaMemsetAsync(E.rb.counter, 0, sizeof(int) * E.P.counters, st));
   if (a.p.timeout_s > 0) {
     count_launch();
     k_set_deadline<<<(E.P.ncols + 127) / 128, 128, 0, st>>>(E.rb.cols, E.P.ncols,
