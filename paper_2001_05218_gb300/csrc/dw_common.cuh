@@ -238,6 +238,80 @@ struct H16<PB16> {
   }
 };
 
+// ------------------------------------------------------------------ 16-bit word arithmetic
+// Operations on 32-bit words holding one complex number as two 16-bit floats
+// (real part in the low half).  pm/rot_pm are packed two-lane adds; cmac and
+// cmac_adj are FP32-accumulating products of 16-bit operands (the product of
+// two 16-bit floats is exact in FP32, so only the accumulation rounds, in FP32).
+// A sign flip of one lane is an XOR of its sign bit.
+constexpr uint32_t kNegRe = 0x00008000u, kNegIm = 0x80000000u, kNegBoth = 0x80008000u;
+
+__device__ __forceinline__ uint32_t swap_halves(uint32_t w) { return __byte_perm(w, 0u, 0x1032); }
+
+template <int P>
+struct HW;
+
+#define DW_HW_SPECIALISE(PREC, TY, PLUS_MINUS, MINUS_PLUS)                                              \
+  template <>                                                                                          \
+  struct HW<PREC> {                                                                                    \
+    /* a + b, a - b per lane */                                                                        \
+    __device__ static __forceinline__ uint32_t add(uint32_t a, uint32_t b) {                           \
+      uint32_t d;                                                                                      \
+      asm("add.rn." TY "x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));                                 \
+      return d;                                                                                        \
+    }                                                                                                  \
+    __device__ static __forceinline__ uint32_t sub(uint32_t a, uint32_t b) {                           \
+      uint32_t d;                                                                                      \
+      asm("sub.rn." TY "x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));                                 \
+      return d;                                                                                        \
+    }                                                                                                  \
+    /* a + T i b (T = +1 or -1): i b = (-b.im, b.re), one rounding per lane */                         \
+    template <int T>                                                                                   \
+    __device__ static __forceinline__ uint32_t rot_add(uint32_t a, uint32_t b) {                       \
+      uint32_t d;                                                                                      \
+      const uint32_t m = T > 0 ? PLUS_MINUS : MINUS_PLUS;                                              \
+      asm("fma.rn." TY "x2 %0, %1, %2, %3;" : "=r"(d) : "r"(swap_halves(b)), "r"(m), "r"(a));         \
+      return d;                                                                                        \
+    }                                                                                                  \
+    /* (re, im) += u h, with hn = h whose imaginary lane is negated */                                 \
+    __device__ static __forceinline__ void cmac(float& re, float& im, uint32_t u, uint32_t h,          \
+                                                uint32_t hn) {                                         \
+      asm("{ .reg .b16 ur, ui, hr, hi, nr, ni;\n\t"                                                 \
+          "mov.b32 {ur, ui}, %2;\n\tmov.b32 {hr, hi}, %3;\n\tmov.b32 {nr, ni}, %4;\n\t"                \
+          "fma.rn.f32." TY " %0, ur, hr, %0;\n\tfma.rn.f32." TY " %0, ui, ni, %0;\n\t"                 \
+          "fma.rn.f32." TY " %1, ur, hi, %1;\n\tfma.rn.f32." TY " %1, ui, hr, %1; }"                  \
+          : "+f"(re), "+f"(im) : "r"(u), "r"(h), "r"(hn));                                             \
+    }                                                                                                  \
+    /* (re, im) += conj(u) h, with hm = h whose real lane is negated */                                \
+    __device__ static __forceinline__ void cmac_adj(float& re, float& im, uint32_t u, uint32_t h,      \
+                                                    uint32_t hm) {                                     \
+      asm("{ .reg .b16 ur, ui, hr, hi, mr, mi;\n\t"                                                 \
+          "mov.b32 {ur, ui}, %2;\n\tmov.b32 {hr, hi}, %3;\n\tmov.b32 {mr, mi}, %4;\n\t"                \
+          "fma.rn.f32." TY " %0, ur, hr, %0;\n\tfma.rn.f32." TY " %0, ui, hi, %0;\n\t"                 \
+          "fma.rn.f32." TY " %1, ur, hi, %1;\n\tfma.rn.f32." TY " %1, ui, mr, %1; }"                  \
+          : "+f"(re), "+f"(im) : "r"(u), "r"(h), "r"(hm));                                             \
+    }                                                                                                  \
+    /* conj(a d - b c) in FP32 from 16-bit words; nc, nd = c, d with both lanes negated */             \
+    __device__ static __forceinline__ void cross(float& re, float& im, uint32_t a, uint32_t b,         \
+                                                 uint32_t c, uint32_t d, uint32_t nc, uint32_t nd) {   \
+      re = 0.f;                                                                                        \
+      im = 0.f;                                                                                        \
+      asm("{ .reg .b16 ar, ai, br, bi, cr, ci, dr, di, ncr, nci, ndr, ndi;\n\t"                     \
+          "mov.b32 {ar, ai}, %2;\n\tmov.b32 {br, bi}, %3;\n\tmov.b32 {cr, ci}, %4;\n\t"                \
+          "mov.b32 {dr, di}, %5;\n\tmov.b32 {ncr, nci}, %6;\n\tmov.b32 {ndr, ndi}, %7;\n\t"            \
+          "fma.rn.f32." TY " %0, ar, dr, %0;\n\tfma.rn.f32." TY " %0, ai, ndi, %0;\n\t"                \
+          "fma.rn.f32." TY " %0, br, ncr, %0;\n\tfma.rn.f32." TY " %0, bi, ci, %0;\n\t"                \
+          "fma.rn.f32." TY " %1, ar, ndi, %1;\n\tfma.rn.f32." TY " %1, ai, ndr, %1;\n\t"               \
+          "fma.rn.f32." TY " %1, br, ci, %1;\n\tfma.rn.f32." TY " %1, bi, cr, %1; }"                  \
+          : "+f"(re), "+f"(im) : "r"(a), "r"(b), "r"(c), "r"(d), "r"(nc), "r"(nd));                    \
+    }                                                                                                  \
+  };
+
+// lane constants (low half first): (-1, +1) and (+1, -1)
+DW_HW_SPECIALISE(P16, "f16", 0x3C00BC00u, 0xBC003C00u)
+DW_HW_SPECIALISE(PB16, "bf16", 0x3F80BF80u, 0xBF803F80u)
+#undef DW_HW_SPECIALISE
+
 // ------------------------------------------------------------------ spinor storage
 template <int P>
 struct Spin;
@@ -316,6 +390,19 @@ struct Spin16 {
       v[4 * k + 1] = cx(c.x, c.y);
       v[4 * k + 2] = cx(d.x, d.y);
       v[4 * k + 3] = cx(e.x, e.y);
+    }
+  }
+  // stored words (one complex per word, see HW) and the site's scale
+  __device__ static __forceinline__ void load_words(const char* base, int vh, int s, uint32_t (&w)[12], float& sc) {
+    const uint4* b = reinterpret_cast<const uint4*>(base);
+    sc = __ldg(reinterpret_cast<const float*>(base + (size_t)48 * vh) + s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const uint4 t = __ldg(b + (size_t)k * vh + s);
+      w[4 * k + 0] = t.x;
+      w[4 * k + 1] = t.y;
+      w[4 * k + 2] = t.z;
+      w[4 * k + 3] = t.w;
     }
   }
   __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&v)[12]) {
@@ -509,6 +596,35 @@ struct Link16 {
       u[6] = cx(g2.x, g2.y);
       u[7] = cx(g3.x, g3.y);
       u[8] = cx(g4.x, g4.y);
+    }
+  }
+  // 16-bit words; with compression the third row is rebuilt from FP32-accumulated
+  // products of the stored rows and rounded once to 16 bits
+  __device__ static __forceinline__ void load_words(const char* base, int vh, int s, uint32_t (&u)[9]) {
+    const uint4 a = __ldg(reinterpret_cast<const uint4*>(base) + s);
+    u[0] = a.x;
+    u[1] = a.y;
+    u[2] = a.z;
+    u[3] = a.w;
+    if (C12) {
+      const uint2 c = __ldg(reinterpret_cast<const uint2*>(base + (size_t)16 * vh) + s);
+      u[4] = c.x;
+      u[5] = c.y;
+      const uint32_t n3 = u[3] ^ kNegBoth, n4 = u[4] ^ kNegBoth, n5 = u[5] ^ kNegBoth;
+      float re, im;
+      HW<P>::cross(re, im, u[1], u[2], u[4], u[5], n4, n5);  // conj(u01 u12 - u02 u11)
+      u[6] = H16<P>::from2(re, im);
+      HW<P>::cross(re, im, u[2], u[0], u[5], u[3], n5, n3);  // conj(u02 u10 - u00 u12)
+      u[7] = H16<P>::from2(re, im);
+      HW<P>::cross(re, im, u[0], u[1], u[3], u[4], n3, n4);  // conj(u00 u11 - u01 u10)
+      u[8] = H16<P>::from2(re, im);
+    } else {
+      const uint4 c = __ldg(reinterpret_cast<const uint4*>(base + (size_t)16 * vh) + s);
+      u[4] = c.x;
+      u[5] = c.y;
+      u[6] = c.z;
+      u[7] = c.w;
+      u[8] = __ldg(reinterpret_cast<const uint32_t*>(base + (size_t)32 * vh) + s);
     }
   }
   __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&u)[9]) {

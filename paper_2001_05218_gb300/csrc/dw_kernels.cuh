@@ -133,6 +133,50 @@ __device__ __forceinline__ void su3_mul(const Cx<R> (&u)[9], const Cx<R> (&h)[6]
     }
 }
 
+// 16-bit operand forms.  The projection runs on packed 16-bit lanes (one
+// extra rounding to 16 bits per half-spinor component); the mat-vec takes the
+// stored 16-bit link and half-spinor components directly into FP32-accumulating
+// fused multiply-adds, so no component is converted to FP32 first.
+template <int MU, int S, int P>
+__device__ __forceinline__ void project_w(const uint32_t (&p)[12], uint32_t (&h)[6]) {
+  using W = HW<P>;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (MU == 0) {        // h0 = p0 - S i p3, h1 = p1 - S i p2
+      h[c] = W::template rot_add<-S>(p[c], p[9 + c]);
+      h[3 + c] = W::template rot_add<-S>(p[3 + c], p[6 + c]);
+    } else if (MU == 1) { // h0 = p0 - S p3, h1 = p1 + S p2
+      h[c] = S > 0 ? W::sub(p[c], p[9 + c]) : W::add(p[c], p[9 + c]);
+      h[3 + c] = S > 0 ? W::add(p[3 + c], p[6 + c]) : W::sub(p[3 + c], p[6 + c]);
+    } else if (MU == 2) { // h0 = p0 - S i p2, h1 = p1 + S i p3
+      h[c] = W::template rot_add<-S>(p[c], p[6 + c]);
+      h[3 + c] = W::template rot_add<S>(p[3 + c], p[9 + c]);
+    } else {              // h0 = p0 + S p2, h1 = p1 + S p3
+      h[c] = S > 0 ? W::add(p[c], p[6 + c]) : W::sub(p[c], p[6 + c]);
+      h[3 + c] = S > 0 ? W::add(p[3 + c], p[9 + c]) : W::sub(p[3 + c], p[9 + c]);
+    }
+  }
+}
+
+template <bool ADJ, int P>
+__device__ __forceinline__ void su3_mul_w(const uint32_t (&u)[9], const uint32_t (&h)[6], Cx<float> (&g)[6]) {
+  uint32_t hx[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) hx[k] = h[k] ^ (ADJ ? kNegRe : kNegIm);
+#pragma unroll
+  for (int k = 0; k < 2; ++k)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float re = 0.f, im = 0.f;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (ADJ) HW<P>::cmac_adj(re, im, u[b * 3 + a], h[3 * k + b], hx[3 * k + b]);
+        else HW<P>::cmac(re, im, u[a * 3 + b], h[3 * k + b], hx[3 * k + b]);
+      }
+      g[3 * k + a] = cx(re, im);
+    }
+}
+
 // Double-float version: each real output is one 6-term dot product.
 template <bool ADJ>
 __device__ __forceinline__ void su3_mul(const Cx<DF> (&u)[9], const Cx<DF> (&h)[6], Cx<DF> (&g)[6]) {
@@ -309,6 +353,11 @@ struct InOne {
     Cx<typename Spin<SP>::R> t[12];
     Spin<SP>::load(slot_ptr(S, slot, r, par), S.vh, s, t);
     convert12(t, v);
+  }
+  // 16-bit storage: stored words and the site scale
+  __device__ __forceinline__ void load_words(const SysDesc& S, int par, int r, int s, uint32_t (&w)[12],
+                                             float& sc) const {
+    Spin<SP>::load_words(slot_ptr(S, slot, r, par), S.vh, s, w, sc);
   }
   // 16-bit storage: unscaled values and the site scale
   template <typename R>
@@ -562,6 +611,32 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
     su3_mul<true>(u, h, g);                                                     \
     accumulate_w<MU, SB>(acc, g, eta < 0.f ? -sc : sc);                         \
   }
+#define DW_HOP_DIR_W(MU)                                                        \
+  {                                                                             \
+    float eta, sc;                                                              \
+    uint32_t p[12], h[6], u[9];                                                 \
+    Cx<float> g[6];                                                             \
+    const int nf = neighbour<MU, +1>(S, c, s, &eta);                            \
+    in.load_words(S, pin, r, nf, p, sc);                                        \
+    project_w<MU, SF, SPA>(p, h);                                               \
+    Link<LP, C12>::load_words(ulink_own + MU * mu_stride, S.vh, s, u);           \
+    su3_mul_w<false, SPA>(u, h, g);                                             \
+    accumulate_w<MU, SF>(acc, g, eta < 0.f ? -sc : sc);                         \
+    const int nb = neighbour<MU, -1>(S, c, s, &eta);                            \
+    in.load_words(S, pin, r, nb, p, sc);                                        \
+    project_w<MU, SB, SPA>(p, h);                                               \
+    Link<LP, C12>::load_words(ulink_nb + MU * mu_stride, S.vh, nb, u);           \
+    su3_mul_w<true, SPA>(u, h, g);                                              \
+    accumulate_w<MU, SB>(acc, g, eta < 0.f ? -sc : sc);                         \
+  }
+#ifndef DW_HOP16_CONVERT
+    if constexpr (SPA == P16 || SPA == PB16) {
+      DW_HOP_DIR_W(0)
+      DW_HOP_DIR_W(1)
+      DW_HOP_DIR_W(2)
+      DW_HOP_DIR_W(3)
+    } else
+#endif
     if constexpr (SPA == PDF) {
       // compact loop: one copy of the double-float mat-vec per (U, U^dag)
 #pragma unroll 1
@@ -599,6 +674,7 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
       DW_HOP_DIR(3)
     }
 #undef DW_HOP_DIR
+#undef DW_HOP_DIR_W
     epi.write(S, par, r, s, acc, nrm);
   }
   if (Epi::kReduce) DW_BLOCK_REDUCE(nrm)

@@ -4,9 +4,10 @@ C ABI against the FP64 oracle on the same seeded inputs.
 Bars: FP64 storage <= 1e-13 and FP32 <= 1e-6 per-site relative norm; the
 double-float format (FP64-sized storage, ~49-bit arithmetic on the FP32
 pipes) is held to the FP64 bar;
-16-bit storage (FP16 / BF16 with FP32 arithmetic) is held to bounds derived
-from the unit roundoff of the storage type (2^-11 for FP16 values scaled to
-[-1, 1] per site, 2^-8 for BF16) times the few roundings on the path.
+16-bit storage (FP16 / BF16 operands, spin projection rounded to 16 bits, FP32
+accumulation) is held to bounds derived from the unit roundoff of the storage
+type (2^-11 for FP16 values scaled to [-1, 1] per site, 2^-8 for BF16) times
+the few roundings on the path.
 Lattices are chosen so that half volumes span several thread blocks and end
 in a partial block (192, 960 and 1620 sites per parity with 128-site blocks).
 """
