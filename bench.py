@@ -278,6 +278,10 @@ def run_suite(args):
     F64 = dict(tol=1e-10, inner="f64", maxiter=100000)
     MIX16 = dict(tol=1e-10, inner="f16", compress12=1, outer="df64", maxiter=100000)
     MIX32 = dict(tol=1e-10, inner="f32", outer="df64", maxiter=100000)
+    if args.delta is not None:
+        MIX16["delta"] = args.delta
+    if args.delta32 is not None:
+        MIX32["delta"] = args.delta32
 
     def zero(*fields):
         for f in fields:
@@ -362,7 +366,9 @@ def main():
     ap.add_argument("--inner", default=None)
     ap.add_argument("--compress12", type=int, default=None)
     ap.add_argument("--outer", default="df64", help="precision of the reliable updates: df64 or f64")
-    ap.add_argument("--delta", type=float, default=None, help="reliable-update threshold (default: automatic)")
+    ap.add_argument("--delta", type=float, default=None,
+                    help="reliable-update threshold (default: automatic); in --suite mode, of the 16-bit solves")
+    ap.add_argument("--delta32", type=float, default=None, help="--suite mode: threshold of the FP32-inner solves")
     ap.add_argument("--impl", default="ours")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -570,7 +576,7 @@ def main():
         "data": "synthetic (seeded exp(i a H) links, Gaussian source)",
         "config": {"workload": wl, "lattice": list(dims), "kappa": kappa, "solver": "even-odd CGNR",
                    "inner": inner, "compress12": c12, "outer": args.outer,
-                   "delta": p_mix.delta if p_mix.delta > 0 else ("auto: 0.03" if inner in ("f16", "bf16") else "auto: 1e-3"),
+                   "delta": p_mix.delta if p_mix.delta > 0 else ("auto: 0.01" if inner in ("f16", "bf16") else "auto: 1e-4"),
                    "certification": "IEEE FP64",
                    "tol": 1e-10, "global_batch": world, "parallelism": "replicas",
                    "l2": "flushed between steps" if flush else "inputs larger than L2 (%d MB working set)" %

@@ -172,9 +172,11 @@ typedef struct {
                           DW_F32/F16/BF16: mixed-precision CG with reliable updates
                           in the `outer` precision */
   double delta;        /* reliable update when |r| < delta * |r at last update|;
-                          0 = by inner precision: 0.03 for FP16/BF16 storage, 1e-3
+                          0 = by inner precision: 0.01 for FP16/BF16 storage, 1e-4
                           for FP32 (the low-precision recursion drifts by about
-                          unit roundoff / delta between corrections) */
+                          unit roundoff / delta between corrections; smaller values
+                          mean fewer high-precision corrections until that drift
+                          starts to cost iterations) */
   int eo;              /* 1: even-odd preconditioned (Schur system on even sites) */
   int compress12;      /* inner-precision links stored as 12 reals */
   int recompute_fwd;   /* dw_cg_backward: 1 = recompute the forward solution */

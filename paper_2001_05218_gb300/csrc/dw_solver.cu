@@ -80,7 +80,7 @@ dw_status solve_many(int n, const dw_field* const* U, const dw_field* const* b, 
     a.x = x + g;
     a.p = *p;
     if (a.p.delta <= 0.0)  // reliable-update threshold by inner precision
-      a.p.delta = (a.p.inner == DW_F16 || a.p.inner == DW_BF16) ? 0.03 : 1e-3;
+      a.p.delta = (a.p.inner == DW_F16 || a.p.inner == DW_BF16) ? 0.01 : 1e-4;
     if (mode == MODE_EO && !p->eo) mode = MODE_FULL;
     a.mode = mode;
     a.stats = stats ? stats + (size_t)g * nrhs : nullptr;
@@ -103,7 +103,7 @@ dw_status dw_solver_params_default(dw_solver_params* p) {
   p->tol = 1e-10;
   p->maxiter = 20000;
   p->inner = DW_F32;
-  p->delta = 0.0;  // automatic: 0.03 for 16-bit inner storage, 1e-3 for FP32
+  p->delta = 0.0;  // automatic: 0.01 for 16-bit inner storage, 1e-4 for FP32
   p->eo = 1;
   p->compress12 = 0;
   p->recompute_fwd = 1;
