@@ -110,16 +110,17 @@ dw_status dw_field_wrap(const dw_lattice* lat, dw_kind kind, dw_prec prec, int c
 dw_status dw_field_free(dw_field* f);
 
 /* Copy host canonical complex128 data into the field (converted to the
- * field's storage precision and layout).  `host` may be pageable or pinned.
- * Pinned (page-locked) memory is read directly by the layout kernel over the
- * host link, asynchronously on `stream`: the buffer must stay valid and
- * unchanged until the stream reaches this point.  Pageable memory is staged
- * through a device buffer. */
+ * field's storage precision and layout): one host-to-device copy into a
+ * staging buffer, then the layout kernel, both on `stream`.  `host` may be
+ * pageable or pinned; from pinned (page-locked) memory the copy is
+ * asynchronous and the buffer must stay valid and unchanged until the stream
+ * reaches this point.  Staging buffers come from a memory pool owned by the
+ * library, which keeps up to 8 GiB per device reserved between calls. */
 dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream);
 
-/* Copy the field back to host canonical complex128 (pinned memory is written
- * directly by the layout kernel).  Data are valid once `stream` has been
- * synchronised. */
+/* Copy the field back to host canonical complex128 (layout kernel into a
+ * staging buffer, then one device-to-host copy).  Data are valid once
+ * `stream` has been synchronised. */
 dw_status dw_field_download(const dw_field* f, double* host, dw_stream_t stream);
 
 /* As upload/download, with the canonical complex128 array in device memory. */

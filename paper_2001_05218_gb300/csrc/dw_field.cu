@@ -627,26 +627,48 @@ dw_status dw_field_export(const dw_field* f, double* dev, dw_stream_t stream) {
   return unpack_spinor_to_canonical(f, dev, st);
 }
 
-// Device-visible address of page-locked host memory (NULL for pageable memory).
-static const void* pinned_device_ptr(const void* host) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
-    cudaGetLastError();
-    return nullptr;
+// Staging buffers for host transfers come from a stream-ordered memory pool
+// owned by the library (one per device), which keeps up to kStagingKeep bytes
+// reserved between calls so that repeated transfers do not reallocate.
+static constexpr uint64_t kStagingKeep = 8ull << 30;
+static std::mutex g_pool_mu;
+static cudaMemPool_t g_pool[64];
+
+static dw_status staging_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  DW_CUDA(cudaGetDevice(&dev));
+  DW_CHECK(dev >= 0 && dev < 64, DW_ERR_ARG, "device index %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof props);
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    DW_CUDA(cudaMemPoolCreate(&p, &props));
+    uint64_t keep = kStagingKeep;
+    DW_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+    g_pool[dev] = p;
   }
-  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  *out = g_pool[dev];
+  return DW_OK;
 }
 
 dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream) {
   DW_CHECK(f != nullptr && host != nullptr, DW_ERR_ARG, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // pinned memory: the layout kernel reads the host array directly
-  if (const void* dp = pinned_device_ptr(host)) return dw_field_import(f, static_cast<const double*>(dp), stream);
+  // one DMA copy into a device staging buffer, then the layout kernel on the
+  // device (measured on a Grace-Blackwell node: about 200 GB/s from pinned
+  // memory, against about 140 GB/s for a kernel reading host memory directly)
   const size_t nb = canonical_bytes(f);
+  cudaMemPool_t pool;
+  DW_TRY(staging_pool(&pool));
   void* tmp = nullptr;
-  DW_CUDA(cudaMallocAsync(&tmp, nb, st));
-  DW_CUDA(cudaMemcpyAsync(tmp, host, nb, cudaMemcpyHostToDevice, st));
-  dw_status s = dw_field_import(f, static_cast<const double*>(tmp), stream);
+  DW_CUDA(cudaMallocFromPoolAsync(&tmp, nb, pool, st));
+  cudaError_t e = cudaMemcpyAsync(tmp, host, nb, cudaMemcpyHostToDevice, st);
+  dw_status s = e == cudaSuccess ? dw_field_import(f, static_cast<const double*>(tmp), stream)
+                                 : cuda_error(e, "cudaMemcpyAsync(host to device)", __FILE__, __LINE__);
   cudaFreeAsync(tmp, st);
   return s;
 }
@@ -654,13 +676,18 @@ dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream) {
 dw_status dw_field_download(const dw_field* f, double* host, dw_stream_t stream) {
   DW_CHECK(f != nullptr && host != nullptr, DW_ERR_ARG, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (const void* dp = pinned_device_ptr(host))
-    return dw_field_export(f, static_cast<double*>(const_cast<void*>(dp)), stream);
+  // layout kernel into a device staging buffer, then one DMA copy (kernel
+  // writes into host memory reach only about a quarter of the DMA rate)
   const size_t nb = canonical_bytes(f);
+  cudaMemPool_t pool;
+  DW_TRY(staging_pool(&pool));
   void* tmp = nullptr;
-  DW_CUDA(cudaMallocAsync(&tmp, nb, st));
+  DW_CUDA(cudaMallocFromPoolAsync(&tmp, nb, pool, st));
   dw_status s = dw_field_export(f, static_cast<double*>(tmp), stream);
-  if (s == DW_OK) DW_CUDA(cudaMemcpyAsync(host, tmp, nb, cudaMemcpyDeviceToHost, st));
+  if (s == DW_OK) {
+    cudaError_t e = cudaMemcpyAsync(host, tmp, nb, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = cuda_error(e, "cudaMemcpyAsync(device to host)", __FILE__, __LINE__);
+  }
   cudaFreeAsync(tmp, st);
   return s;
 }
