@@ -86,30 +86,49 @@ class ClockSampler:
         self.lines = []
 
     def start(self):
+        """Starts sampling every 50 ms and waits (up to 5 s) for the first
+        sample, so that the region marked next is covered from its start."""
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.monotonic() + 5.0
+            while not self.lines and time.monotonic() < t_end and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark(self):
+        """Start of the timed region."""
+        self.t0 = time.monotonic()
 
     def stop(self):
+        """Samples taken between mark() and now (plus the one that follows)."""
+        t1 = time.monotonic()
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t_end = t1 + 0.5
+        while not any(t >= t1 for t, _ in self.lines) and time.monotonic() < t_end:
+            time.sleep(0.01)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
+        t0 = getattr(self, "t0", 0.0)
+        after = [t for t, _ in self.lines if t >= t1]
+        t_last = min(after) if after else t1
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if t < t0 or t > t_last:
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -435,6 +454,7 @@ def main():
     barrier()
     clk = ClockSampler(local)
     clk.start()
+    clk.mark()
     stream = torch.cuda.current_stream()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     dw.profile_start(time_stencils=False)  # counts kernel executions; the solver loop stays a CUDA graph
