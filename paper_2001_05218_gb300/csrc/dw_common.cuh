@@ -891,6 +891,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// Warp total in lane 0 only (other lanes hold partial sums), fixed order.  Only
+// the lanes whose partial is still needed add, 31 FP64 additions per warp
+// instead of the butterfly's 160: GB300 executes two FP64 thread operations per
+// clock per SM, so the butterfly alone cost several microseconds per launch.
+__device__ __forceinline__ double warp_sum_lane0(double v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_down_sync(0xffffffffu, v, o);
+    if (lane < o) v += t;
+  }
+  return v;
+}
 
 // Two-level deterministic grid reduction.  A block holds RB groups of T
 // threads (T a multiple of 32); group g works on right-hand side
@@ -947,7 +960,7 @@ __device__ __forceinline__ void reduce_finalize(const SysDesc& S, int T, int RB,
   __shared__ double wsum[32];
   __shared__ int am_last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  v = warp_sum(v);
+  v = warp_sum_lane0(v);
   if (lane == 0) wsum[warp] = v;
   __syncthreads();
   const int wpr = T >> 5;
@@ -958,8 +971,11 @@ __device__ __forceinline__ void reduce_finalize(const SysDesc& S, int T, int RB,
       for (int w = 0; w < wpr; ++w) s += wsum[tid * wpr + w];
       ra.partial[S.part0 + r * ntiles + tile] = s;
     }
+    // only the writers of partials fence (before thread 0's arrival below):
+    // a fence in every thread would hold each thread until its own output
+    // stores were acknowledged
+    __threadfence();
   }
-  __threadfence();
   __syncthreads();
   const int g = tile / kRedGroup;
   const int ngroups = (ntiles + kRedGroup - 1) / kRedGroup;
