@@ -167,6 +167,51 @@ __device__ __forceinline__ DF df_dot6(const DF (&x)[6], const DF (&y)[6]) {
 }
 
 
+// Two independent double-float numbers in the two lanes of packed FP32x2
+// registers: each instruction below does the same IEEE operation on both
+// lanes (Blackwell's fma/add/mul.rn.f32x2), so one sequence computes two
+// double-float results.  Same algorithms as the scalar forms above.
+struct DF2 {
+  float2 hi, lo;
+};
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, bc2(-1.f), a); }
+// a + b exactly as s + e, lane by lane (Knuth)
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  const float2 bb = sub2(s, a);
+  e = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// x * y for a double-float x (same in both lanes) and two double-floats y:
+// exact high product p and the low-order terms e, x*y = p + e (+ x.lo*y.lo)
+__device__ __forceinline__ void prod_terms2(DF x, const DF2& y, float2& p, float2& e) {
+  const float2 xh = bc2(x.hi);
+  p = __fmul2_rn(xh, y.hi);
+  e = __ffma2_rn(xh, y.hi, make_float2(-p.x, -p.y));
+  e = __ffma2_rn(xh, y.lo, e);
+  e = __ffma2_rn(bc2(x.lo), y.hi, e);
+}
+// Two six-term dot products sum_i x_i * y_i (lane-wise in y), as df_dot6.
+__device__ __forceinline__ DF2 df2_dot6(const DF (&x)[6], const DF2 (&y)[6]) {
+  float2 p[6], e[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) prod_terms2(x[i], y[i], p[i], e[i]);
+  float2 ab, abe, cd, cde, ef, efe, abcd, abcde, all, alle;
+  two_sum2(p[0], p[1], ab, abe);
+  two_sum2(p[2], p[3], cd, cde);
+  two_sum2(p[4], p[5], ef, efe);
+  two_sum2(ab, cd, abcd, abcde);
+  two_sum2(abcd, ef, all, alle);
+  const float2 lo1 = __fadd2_rn(__fadd2_rn(e[0], e[1]), __fadd2_rn(e[2], e[3]));
+  const float2 lo2 = __fadd2_rn(__fadd2_rn(e[4], e[5]), __fadd2_rn(abe, cde));
+  const float2 lo3 = __fadd2_rn(__fadd2_rn(efe, abcde), alle);
+  const float2 lo = __fadd2_rn(__fadd2_rn(lo1, lo2), lo3);
+  DF2 r;
+  r.hi = __fadd2_rn(all, lo);
+  r.lo = sub2(lo, sub2(r.hi, all));
+  return r;
+}
+
 // ------------------------------------------------------------------ complex
 template <typename R>
 struct Cx {

@@ -177,7 +177,52 @@ __device__ __forceinline__ void su3_mul_w(const uint32_t (&u)[9], const uint32_t
     }
 }
 
-// Double-float version: each real output is one 6-term dot product.
+// Double-float version: each real output is one 6-term dot product.  The two
+// spin rows of the half spinor are the two lanes of packed FP32x2 arithmetic,
+// so each packed dot product yields one real output for both rows.
+#ifndef DW_DF_PACKED
+#define DW_DF_PACKED 1
+#endif
+#if DW_DF_PACKED
+template <bool ADJ>
+__device__ __forceinline__ void su3_mul(const Cx<DF> (&u)[9], const Cx<DF> (&h)[6], Cx<DF> (&g)[6]) {
+  DF2 hr[3], hi[3], hrn[3], hin[3];  // rows k = 0, 1 in the lanes; n: negated
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    hr[b].hi = make_float2(h[b].re.hi, h[3 + b].re.hi);
+    hr[b].lo = make_float2(h[b].re.lo, h[3 + b].re.lo);
+    hi[b].hi = make_float2(h[b].im.hi, h[3 + b].im.hi);
+    hi[b].lo = make_float2(h[b].im.lo, h[3 + b].im.lo);
+    hrn[b].hi = make_float2(-hr[b].hi.x, -hr[b].hi.y);
+    hrn[b].lo = make_float2(-hr[b].lo.x, -hr[b].lo.y);
+    hin[b].hi = make_float2(-hi[b].hi.x, -hi[b].hi.y);
+    hin[b].lo = make_float2(-hi[b].lo.x, -hi[b].lo.y);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    DF xr[6], xi[6];
+    DF2 yr[6], yi[6];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const Cx<DF> m = ADJ ? u[b * 3 + a] : u[a * 3 + b];
+      // re = m.re h.re -/+ m.im h.im ; im = m.re h.im +/- m.im h.re  (lower sign: adjoint)
+      xr[2 * b] = m.re;
+      yr[2 * b] = hr[b];
+      xr[2 * b + 1] = m.im;
+      yr[2 * b + 1] = ADJ ? hi[b] : hin[b];
+      xi[2 * b] = m.re;
+      yi[2 * b] = hi[b];
+      xi[2 * b + 1] = m.im;
+      yi[2 * b + 1] = ADJ ? hrn[b] : hr[b];
+    }
+    const DF2 re = df2_dot6(xr, yr), im = df2_dot6(xi, yi);
+    g[a].re = df_make(re.hi.x, re.lo.x);
+    g[a].im = df_make(im.hi.x, im.lo.x);
+    g[3 + a].re = df_make(re.hi.y, re.lo.y);
+    g[3 + a].im = df_make(im.hi.y, im.lo.y);
+  }
+}
+#else
 template <bool ADJ>
 __device__ __forceinline__ void su3_mul(const Cx<DF> (&u)[9], const Cx<DF> (&h)[6], Cx<DF> (&g)[6]) {
 #pragma unroll
@@ -203,6 +248,7 @@ __device__ __forceinline__ void su3_mul(const Cx<DF> (&u)[9], const Cx<DF> (&h)[
       g[3 * k + a].im = df_dot6(xi, yi);
     }
 }
+#endif
 
 // Runtime-direction form of the spin projection and reconstruction, used by
 // the double-float stencil whose unrolled body would not fit the instruction
