@@ -23,18 +23,19 @@ BlockShape tune_inner_shape(const std::vector<dw_lattice>& lats, int nrhs, const
     snprintf(dev_name, sizeof dev_name, "%s", prop.name);
   for (char* c = dev_name; *c; ++c)
     if (*c == ' ') *c = '_';
-  std::string key = std::string(dev_name) + "/v2/" + prec_name(L) + (C12 ? "c12" : "c18") + "/r" + std::to_string(nrhs);
+  std::string key = std::string(dev_name) + "/v3/" + prec_name(L) + (C12 ? "c12" : "c18") + "/r" + std::to_string(nrhs);
   for (auto& l : lats)
     key += "/" + std::to_string(l.dims[0]) + "x" + std::to_string(l.dims[1]) + "x" + std::to_string(l.dims[2]) +
            "x" + std::to_string(l.dims[3]);
   BlockShape best{0, 0};
   if (tune_lookup(key, &best)) return best;
 
-  // candidates: 64..256 sites per block; with several right-hand sides, RB of
-  // them share a block (and its link loads through L1).  Blocks narrower than
-  // 64 sites multiply the reduction partials and are not offered.
+  // candidates: 32..256 sites per block; with several right-hand sides, RB of
+  // them share a block (and its link loads through L1).  32-site blocks spread
+  // small lattices over more SMs, which matters most where one SM's FP64 pipe
+  // (two operations per clock on GB300) would otherwise carry a whole lattice.
   std::vector<BlockShape> cand;
-  for (int T : {64, 128, 256})
+  for (int T : {32, 64, 128, 256})
     for (int RB = 1; RB <= nrhs && RB <= 12; ++RB)
       if (nrhs % RB == 0 && T * RB <= 256) cand.push_back(BlockShape{T, RB});
 
