@@ -32,6 +32,9 @@
  *     handed to dw_field_wrap stays owned by the caller and must outlive the
  *     field handle.
  *   - dw_last_error() returns a thread-local message for the last failure.
+ *   - Solver calls (dw_cg_solve*, dw_cg_backward) from several host threads
+ *     are serialised within a process: they share the cache of solver plans
+ *     and working memory.
  *   - Dimensions must all be even and Lx*Ly*Lz*Lt/2 must be a multiple of 8.
  *
  * Host canonical layout (complex128 as interleaved re, im doubles):

@@ -1,4 +1,6 @@
 // dw_solver.cu -- C ABI of the solvers: argument checks and precision dispatch.
+#include <mutex>
+
 #include "dw_solver.cuh"
 
 namespace dw {
@@ -65,8 +67,15 @@ static dw_status check_system(const dw_field* U, const dw_field* b, const dw_fie
   return DW_OK;
 }
 
+// Solves share process-wide state (the plan cache, whose eviction frees the
+// working memory of an entry, the tuning cache and the cached link copies on
+// the gauge handles), so they run one at a time per process.  Recursive: the
+// adjoint solver calls back into this function.
+static std::recursive_mutex g_solve_mu;
+
 dw_status solve_many(int n, const dw_field* const* U, const dw_field* const* b, dw_field* const* x,
                      const dw_solver_params* p, dw_solver_stats* stats, cudaStream_t st, int mode) {
+  std::lock_guard<std::recursive_mutex> lock(g_solve_mu);
   DW_CHECK(n >= 1 && U && b && x, DW_ERR_ARG, "need n >= 1 systems and non-NULL arrays");
   DW_TRY(check_params(p));
   const int nrhs = b[0] ? b[0]->nrhs : 0;

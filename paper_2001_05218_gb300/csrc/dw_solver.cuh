@@ -494,7 +494,7 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
                                                  : -1.0;
         o.time_ms = ms;
         const double vh = (double)S.vh;
-        const double hops_lo = (mode == MODE_EO ? 4.0 : 4.0) * c.iter;  // parity-hops per iteration
+        const double hops_lo = 4.0 * c.iter;  // parity-hops per iteration (D and D^dag, two each)
         const double hops_hi = 2.0 * c.nrel + 6.0;
         o.flops = 1320.0 * vh * (hops_lo + hops_hi);
         const double lo_hop = 8.0 * link_bytes(L, C12) + 2.0 * spin_bytes(L);

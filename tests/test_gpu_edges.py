@@ -160,3 +160,42 @@ def test_tuning_cache_file_round_trip(dw, tmp_path, monkeypatch):
     for key, T, RB in lines:
         T, RB = int(T), int(RB)
         assert T % 32 == 0 and 64 <= T <= 256 and RB >= 1 and T * RB <= 256
+
+
+def test_solves_from_two_host_threads(dw):
+    """Solver calls from two host threads (different systems, precisions and
+    lattices, hence different cached plans) are serialised by the library and
+    both certify against the oracle."""
+    import threading
+    import torch
+    cases = [((4, 4, 4, 8), 0.12, 101, dict(inner="f16", compress12=1, outer="df64")),
+             ((6, 4, 4, 6), 0.118, 102, dict(inner="f32", outer="f64"))]
+    fields = []
+    for dims, kappa, seed, kw in cases:
+        U = I.gauge_field(dims, "exp", seed, 1, 0.4)
+        b = I.gaussian_spinor(dims, seed, 2)
+        fields.append((dims, kappa, U, b, dw.gauge(dims, kappa, U), dw.spinor(dims, b), dw.spinor(dims),
+                       dw.params(tol=1e-10, **kw)))
+    torch.cuda.synchronize()
+    out, errs = {}, []
+
+    def worker(i):
+        try:
+            torch.cuda.set_device(0)
+            dims, kappa, U, b, Ug, bg, xg, p = fields[i]
+            for _ in range(3):
+                xg.storage.zero_()
+                s, st = dw.cg_solve(Ug, bg, xg, p)
+                assert s == dw.DW_OK
+            out[i] = xg.download()
+        except Exception as e:  # reported below
+            errs.append(repr(e))
+
+    th = [threading.Thread(target=worker, args=(i,)) for i in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errs, errs
+    for i, (dims, kappa, U, b, *_rest) in enumerate(fields):
+        assert _resid(dims, kappa, U, out[i], b) <= 1e-10
