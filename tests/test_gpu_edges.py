@@ -159,7 +159,7 @@ def test_tuning_cache_file_round_trip(dw, tmp_path, monkeypatch):
     assert lines
     for key, T, RB in lines:
         T, RB = int(T), int(RB)
-        assert T % 32 == 0 and 64 <= T <= 256 and RB >= 1 and T * RB <= 256
+        assert T % 32 == 0 and 32 <= T <= 256 and RB >= 1 and T * RB <= 256
 
 
 def test_solves_from_two_host_threads(dw):
