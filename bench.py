@@ -238,7 +238,7 @@ def run_dslash(args):
     from paper_2001_05218_gb300 import dw
     from paper_2001_05218_gb300 import inputs as I
     prec = dw.PREC[args.dslash]
-    c12 = args.compress12 if args.compress12 is not None else (1 if args.dslash in ("f16", "bf16") else 0)
+    c12 = args.compress12 if args.compress12 is not None else (1 if args.dslash in ("f16", "bf16", "i16") else 0)
     dims, kappa, U, b = I.make_workload(args.workload)
     V = int(np.prod(dims))
     s = np.arange(V)
@@ -297,6 +297,7 @@ def run_suite(args):
     F64 = dict(tol=1e-10, inner="f64", maxiter=100000)
     MIX16 = dict(tol=1e-10, inner="f16", compress12=1, outer="df64", maxiter=100000)
     MIX32 = dict(tol=1e-10, inner="f32", outer="df64", maxiter=100000)
+    MIXI16 = dict(tol=1e-10, inner="i16", compress12=1, outer="df64", maxiter=100000)
     if args.delta is not None:
         MIX16["delta"] = args.delta
     if args.delta32 is not None:
@@ -321,7 +322,14 @@ def run_suite(args):
                                                                  ("f64_eo", F64)])
     out["wilson_16x16x16x32_exp0.4"] = single("wilson_16x16x16x32_exp0.4", [
         ("f64", F64), ("df64", dict(tol=1e-10, inner="df64")), ("f32_mixed", MIX32), ("f16_mixed", MIX16),
-        ("f32_defect_correction", dict(MIX32, defect_correction=1))])
+        ("f32_defect_correction", dict(MIX32, defect_correction=1)),
+        # 12- against 18-real links in the FP32 inner solve, and the full-lattice
+        # (not even-odd) CGNR, whose operator uses every link twice per launch
+        ("f32_mixed_12real_links", dict(MIX32, compress12=1)), ("i16_mixed", MIXI16),
+        ("f64_full_lattice", dict(F64, eo=0)), ("f16_mixed_full_lattice", dict(MIX16, eo=0))])
+    out["wilson_32x32x32x64_exp0.6"] = single("wilson_32x32x32x64_exp0.6", [
+        ("f16_mixed_eo", MIX16), ("f16_mixed_full_lattice", dict(MIX16, eo=0)),
+        ("f32_mixed_eo", MIX32), ("f32_mixed_12real_links", dict(MIX32, compress12=1)), ("i16_mixed_eo", MIXI16)])
     # 12 point sources on 24^3x48: one multi-RHS solve vs 12 single solves
     name = "wilson_24x24x24x48_exp0.4_12src"
     dims, kappa, U, _ = I.make_workload(name, with_source=False)
@@ -392,7 +400,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--dslash", default=None, help="stencil-only mode: f64|f32|f16|bf16|df64 (Schur operator applies)")
+    ap.add_argument("--dslash", default=None, help="stencil-only mode: f64|f32|f16|bf16|i16|df64 (Schur operator applies)")
     ap.add_argument("--nrhs", type=int, default=1, help="stencil-only mode: right-hand sides per field")
     ap.add_argument("--suite", action="store_true", help="time every workload configuration (not the benchmark line)")
     args = ap.parse_args()

@@ -72,7 +72,13 @@ typedef enum {
  * numbers (about 49 significant bits) with double-float arithmetic on the
  * FP32 pipes; same size as FP64.  On GB300 the FP64 pipe runs at 1/61 of the
  * FP32 rate, so FP64-class stencils are faster this way. */
-typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3, DW_DF64 = 4 } dw_prec;
+/* DW_I16: 16-bit fixed point.  Spinor components are stored as
+ * round(32767 * value / max|component of the site|) with one FP32 scale per
+ * site (the layout of FP16 storage); link entries, which SU(3) bounds by 1 in
+ * magnitude, as round(32767 * entry).  Arithmetic in FP32.  Relative
+ * resolution 2^-15 of the site's largest component, against FP16's 2^-11 of
+ * each value. */
+typedef enum { DW_F64 = 0, DW_F32 = 1, DW_F16 = 2, DW_BF16 = 3, DW_DF64 = 4, DW_I16 = 5 } dw_prec;
 
 typedef enum {
   DW_GAUGE = 0,       /* links U_mu(x), all sites */
@@ -139,7 +145,8 @@ dw_status dw_field_info(const dw_field* f, dw_lattice* lat, dw_kind* kind, dw_pr
 /* out = D in.  in/out FULL: the operator on all sites.  in/out EVEN (ODD):
  * the Schur complement on that parity, 1 - kappa^2 H_pq H_qp.  U, in and out
  * share one storage precision (FP64: IEEE binary64 throughout; FP32: binary32;
- * FP16/BF16: 16-bit storage with FP32 arithmetic).  kappa and the boundary
+ * FP16/BF16: 16-bit storage, 16-bit operands, FP32 accumulation; I16:
+ * 16-bit fixed point with FP32 arithmetic).  kappa and the boundary
  * condition come from U's lattice.  in and out must not alias. */
 dw_status dw_apply(const dw_field* U, const dw_field* in, dw_field* out, dw_stream_t stream);
 
@@ -158,7 +165,7 @@ dw_status dw_normal_apply(const dw_field* U, const dw_field* in, dw_field* out, 
  * The Schur complement's intermediate parity field goes to one fixed 32 MiB
  * array in device memory that the library reserves on every GPU that loads
  * it, until the process exits.  Limit: nrhs * Vh * (bytes per site of the
- * storage precision: 192 FP64, 96 FP32, 52 FP16/BF16) <= 32 MiB; larger
+ * storage precision: 192 FP64, 96 FP32, 52 FP16/BF16/I16) <= 32 MiB; larger
  * fields return DW_ERR_SHAPE with nothing enqueued (FULL fields need no
  * scratch).  All calls on a device share the array, which keeps the last
  * call's contents; calls whose kernels can run at the same time on the GPU
@@ -173,11 +180,11 @@ typedef struct {
   double tol;          /* stop when |b - D x| / |b| <= tol, recomputed in FP64 */
   int maxiter;         /* CG iteration limit */
   dw_prec inner;       /* DW_F64: plain FP64 CG.  DW_DF64: plain CG in double-float.
-                          DW_F32/F16/BF16: mixed-precision CG with reliable updates
+                          DW_F32/F16/BF16/I16: mixed-precision CG with reliable updates
                           in the `outer` precision */
   double delta;        /* reliable update when |r| < delta * |r at last update|;
-                          0 = by inner precision: 0.01 for FP16/BF16 storage, 1e-4
-                          for FP32 (the low-precision recursion drifts by about
+                          0 = by inner precision: 0.01 for FP16/BF16 storage, 1e-3
+                          for I16, 1e-4 for FP32 (the low-precision recursion drifts by about
                           unit roundoff / delta between corrections; smaller values
                           mean fewer high-precision corrections until that drift
                           starts to cost iterations) */

@@ -9,11 +9,14 @@
 //   spinor FP32 :  6 planes of float4        (complex 2j, 2j+1)
 //   spinor F16/BF16: 3 planes of 8 halves (uint4) + 1 plane of FP32 per-site
 //                  scale; stored value = component / max|component of site|
+//   spinor I16   : the same planes of 16-bit fixed point: round(32767 *
+//                  component / max|component of site|), FP32 per-site scale
 //   links  (parity p of the base site, direction mu) planes of
 //          FP64 18: 9 double2   FP64 12: 6 double2
 //          FP32 18: 9 float2    FP32 12: 3 float4
 //          F16/BF16 18: uint4, uint4, uint (18 halves)
 //          F16/BF16 12: uint4, uint2 (12 halves)
+//          I16 as F16/BF16, each entry stored as round(32767 * entry)
 //   12-real links keep rows 0 and 1; row 2 = conj(row0 x row1) (SU(3)).
 #pragma once
 
@@ -24,7 +27,7 @@
 
 namespace dw {
 
-enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PDF = 4 };
+enum Prec { P64 = 0, P32 = 1, P16 = 2, PB16 = 3, PDF = 4, PI16 = 5 };
 
 // ------------------------------------------------------------------ double-float
 // A real as the unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2),
@@ -262,6 +265,7 @@ template <int P>
 struct H16;
 template <>
 struct H16<P16> {
+  static constexpr float kUnit = 1.f;  // stored units per 1
   __device__ static __forceinline__ float2 to2(uint32_t w) {
     __half2 h = *reinterpret_cast<__half2*>(&w);
     return __half22float2(h);
@@ -273,6 +277,7 @@ struct H16<P16> {
 };
 template <>
 struct H16<PB16> {
+  static constexpr float kUnit = 1.f;
   __device__ static __forceinline__ float2 to2(uint32_t w) {
     __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
     return __bfloat1622float2(h);
@@ -280,6 +285,24 @@ struct H16<PB16> {
   __device__ static __forceinline__ uint32_t from2(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+
+// 16-bit fixed point: q = round(32767 x) for x in [-1, 1], two per word
+// (first value in the low half).  to2 returns the integers q themselves
+// (kUnit = 32767 units per 1), so the unit folds into the per-site scale.
+// (Exact bit-level conversions on the FP32/ALU pipes were measured slower
+// than the conversion instructions.)
+template <>
+struct H16<PI16> {
+  static constexpr float kUnit = 32767.f;
+  __device__ static __forceinline__ float2 to2(uint32_t w) {
+    return make_float2(__int2float_rn((int)(short)(w & 0xFFFFu)), __int2float_rn((int)w >> 16));
+  }
+  // a, b in [-1, 1] (values already divided by their site maximum)
+  __device__ static __forceinline__ uint32_t from2(float a, float b) {
+    const int qa = __float2int_rn(a * 32767.f), qb = __float2int_rn(b * 32767.f);
+    return ((uint32_t)qa & 0xFFFFu) | ((uint32_t)qb << 16);
   }
 };
 
@@ -423,10 +446,11 @@ struct Spin16 {
   using R = float;
   static constexpr bool kScaled = true;
   static constexpr int kBytes = 52;  // 48 bytes of halves + 4 bytes of scale
-  // stored values (unscaled) and the site's scale: value = v * scale
+  // stored values (unscaled, in stored units) and the site's scale per unit:
+  // value = v * sc
   __device__ static __forceinline__ void load_raw(const char* base, int vh, int s, Cx<float> (&v)[12], float& sc) {
     const uint4* b = reinterpret_cast<const uint4*>(base);
-    sc = __ldg(reinterpret_cast<const float*>(base + (size_t)48 * vh) + s);
+    sc = __ldg(reinterpret_cast<const float*>(base + (size_t)48 * vh) + s) * (1.f / H16<P>::kUnit);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       uint4 t = __ldg(b + (size_t)k * vh + s);
@@ -452,7 +476,7 @@ struct Spin16 {
   }
   __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&v)[12]) {
     const uint4* b = reinterpret_cast<const uint4*>(base);
-    const float sc = __ldg(reinterpret_cast<const float*>(base + (size_t)48 * vh) + s);
+    const float sc = __ldg(reinterpret_cast<const float*>(base + (size_t)48 * vh) + s) * (1.f / H16<P>::kUnit);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       uint4 t = __ldg(b + (size_t)k * vh + s);
@@ -481,10 +505,11 @@ struct Spin16 {
   __device__ static __forceinline__ void roundtrip(Cx<float> (&v)[12]) {
     const float m = site_max(v);
     const float inv = m > 0.f ? 1.0f / m : 0.f;
+    const float mu = m * (1.f / H16<P>::kUnit);
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       float2 q = H16<P>::to2(H16<P>::from2(v[k].re * inv, v[k].im * inv));
-      v[k] = cx(q.x * m, q.y * m);
+      v[k] = cx(q.x * mu, q.y * mu);
     }
   }
 };
@@ -492,6 +517,8 @@ template <>
 struct Spin<P16> : Spin16<P16> {};
 template <>
 struct Spin<PB16> : Spin16<PB16> {};
+template <>
+struct Spin<PI16> : Spin16<PI16> {};
 
 // double-float: 12 planes of float4 (re.hi, re.lo, im.hi, im.lo)
 template <>
@@ -619,28 +646,29 @@ struct Link16 {
   using R = float;
   static constexpr int kBytes = C12 ? 24 : 36;
   __device__ static __forceinline__ void load(const char* base, int vh, int s, Cx<float> (&u)[9]) {
+    constexpr float k = 1.f / H16<P>::kUnit;  // stored units -> entry
     const uint4 a = __ldg(reinterpret_cast<const uint4*>(base) + s);
     float2 f0 = H16<P>::to2(a.x), f1 = H16<P>::to2(a.y), f2 = H16<P>::to2(a.z), f3 = H16<P>::to2(a.w);
-    u[0] = cx(f0.x, f0.y);
-    u[1] = cx(f1.x, f1.y);
-    u[2] = cx(f2.x, f2.y);
-    u[3] = cx(f3.x, f3.y);
+    u[0] = cx(f0.x * k, f0.y * k);
+    u[1] = cx(f1.x * k, f1.y * k);
+    u[2] = cx(f2.x * k, f2.y * k);
+    u[3] = cx(f3.x * k, f3.y * k);
     if (C12) {
       const uint2 c = __ldg(reinterpret_cast<const uint2*>(base + (size_t)16 * vh) + s);
       float2 g0 = H16<P>::to2(c.x), g1 = H16<P>::to2(c.y);
-      u[4] = cx(g0.x, g0.y);
-      u[5] = cx(g1.x, g1.y);
+      u[4] = cx(g0.x * k, g0.y * k);
+      u[5] = cx(g1.x * k, g1.y * k);
       rebuild_row2(u);
     } else {
       const uint4 c = __ldg(reinterpret_cast<const uint4*>(base + (size_t)16 * vh) + s);
       const uint32_t d = __ldg(reinterpret_cast<const uint32_t*>(base + (size_t)32 * vh) + s);
       float2 g0 = H16<P>::to2(c.x), g1 = H16<P>::to2(c.y), g2 = H16<P>::to2(c.z), g3 = H16<P>::to2(c.w);
       float2 g4 = H16<P>::to2(d);
-      u[4] = cx(g0.x, g0.y);
-      u[5] = cx(g1.x, g1.y);
-      u[6] = cx(g2.x, g2.y);
-      u[7] = cx(g3.x, g3.y);
-      u[8] = cx(g4.x, g4.y);
+      u[4] = cx(g0.x * k, g0.y * k);
+      u[5] = cx(g1.x * k, g1.y * k);
+      u[6] = cx(g2.x * k, g2.y * k);
+      u[7] = cx(g3.x * k, g3.y * k);
+      u[8] = cx(g4.x * k, g4.y * k);
     }
   }
   // 16-bit words; with compression the third row is rebuilt from FP32-accumulated
@@ -699,6 +727,8 @@ template <bool C12>
 struct Link<P16, C12> : Link16<P16, C12> {};
 template <bool C12>
 struct Link<PB16, C12> : Link16<PB16, C12> {};
+template <bool C12>
+struct Link<PI16, C12> : Link16<PI16, C12> {};
 
 // ------------------------------------------------------------------ descriptors
 // A field reference inside a system: address of (rhs r, parity par) block is

@@ -46,7 +46,7 @@ inline void count_launch() {
   if (p.on) p.launches += 1;
 }
 inline const char* prec_name(int p) {
-  return p == P64 ? "f64" : p == P32 ? "f32" : p == P16 ? "f16" : p == PB16 ? "bf16" : "df64";
+  return p == P64 ? "f64" : p == P32 ? "f32" : p == P16 ? "f16" : p == PB16 ? "bf16" : p == PI16 ? "i16" : "df64";
 }
 
 struct Exec {

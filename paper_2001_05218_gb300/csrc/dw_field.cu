@@ -38,6 +38,7 @@ int spin_bytes(int prec) {
     case DW_F16: return Spin<P16>::kBytes;
     case DW_BF16: return Spin<PB16>::kBytes;
     case DW_DF64: return Spin<PDF>::kBytes;
+    case DW_I16: return Spin<PI16>::kBytes;
   }
   return 0;
 }
@@ -49,6 +50,7 @@ int link_bytes(int prec, int c12) {
     case DW_F16: return c12 ? Link<P16, true>::kBytes : Link<P16, false>::kBytes;
     case DW_BF16: return c12 ? Link<PB16, true>::kBytes : Link<PB16, false>::kBytes;
     case DW_DF64: return c12 ? Link<PDF, true>::kBytes : Link<PDF, false>::kBytes;
+    case DW_I16: return c12 ? Link<PI16, true>::kBytes : Link<PI16, false>::kBytes;
   }
   return 0;
 }
@@ -303,6 +305,7 @@ static Dims4 dims4(const dw_lattice& l) {
     case DW_F16: { constexpr int PP = P16; BODY; } break;  \
     case DW_BF16: { constexpr int PP = PB16; BODY; } break; \
     case DW_DF64: { constexpr int PP = PDF; BODY; } break; \
+    case DW_I16: { constexpr int PP = PI16; BODY; } break; \
   }
 
 dw_status pack_spinor_from_canonical(dw_field* f, const double* dev, cudaStream_t st) {
@@ -530,7 +533,7 @@ dw_status dw_field_bytes(const dw_lattice* lat, dw_kind kind, dw_prec prec, int 
                          size_t* bytes) {
   DW_TRY(check_lattice(lat));
   DW_CHECK(bytes != nullptr, DW_ERR_ARG, "bytes is NULL");
-  DW_CHECK(prec >= DW_F64 && prec <= DW_DF64, DW_ERR_PRECISION, "unknown precision %d", (int)prec);
+  DW_CHECK(prec >= DW_F64 && prec <= DW_I16, DW_ERR_PRECISION, "unknown precision %d", (int)prec);
   DW_CHECK(kind >= DW_GAUGE && kind <= DW_SPINOR_ODD, DW_ERR_ARG, "unknown field kind %d", (int)kind);
   const long long vh = vh_of(*lat);
   if (kind == DW_GAUGE) {

@@ -122,6 +122,7 @@ extern "C" dw_status dw_apply_noalloc(const dw_field* U, const dw_field* in, dw_
     case DW_F16: DW_NOALLOC_CASE(P16) break;
     case DW_BF16: DW_NOALLOC_CASE(PB16) break;
     case DW_DF64: DW_NOALLOC_CASE(PDF) break;
+    case DW_I16: DW_NOALLOC_CASE(PI16) break;
   }
 #undef DW_NOALLOC_CASE
   DW_CUDA(cudaGetLastError());

@@ -62,6 +62,7 @@ static dw_status apply_one(const dw_field* U, const dw_field* in, dw_field* out,
     case DW_F16: DW_APPLY_CASE(P16) break;
     case DW_BF16: DW_APPLY_CASE(PB16) break;
     case DW_DF64: DW_APPLY_CASE(PDF) break;
+    case DW_I16: DW_APPLY_CASE(PI16) break;
   }
 #undef DW_APPLY_CASE
   cudaError_t e = cudaGetLastError();

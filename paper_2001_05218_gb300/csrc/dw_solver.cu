@@ -20,6 +20,10 @@ DW_CG_EXTERN(P16, P32, false, PDF)
 DW_CG_EXTERN(P16, P32, true, PDF)
 DW_CG_EXTERN(PB16, P32, false, PDF)
 DW_CG_EXTERN(PB16, P32, true, PDF)
+DW_CG_EXTERN(PI16, P32, false, P64)
+DW_CG_EXTERN(PI16, P32, true, P64)
+DW_CG_EXTERN(PI16, P32, false, PDF)
+DW_CG_EXTERN(PI16, P32, true, PDF)
 #undef DW_CG_EXTERN
 
 template <int H>
@@ -29,6 +33,7 @@ static dw_status dispatch_inner(const SolveArgs& a) {
     case DW_F32: return c ? CG<P32, P32, true, H>::run(a) : CG<P32, P32, false, H>::run(a);
     case DW_F16: return c ? CG<P16, P32, true, H>::run(a) : CG<P16, P32, false, H>::run(a);
     case DW_BF16: return c ? CG<PB16, P32, true, H>::run(a) : CG<PB16, P32, false, H>::run(a);
+    case DW_I16: return c ? CG<PI16, P32, true, H>::run(a) : CG<PI16, P32, false, H>::run(a);
     default: break;
   }
   return set_error(DW_ERR_PRECISION, "unknown inner precision %d", (int)a.p.inner);
@@ -44,7 +49,7 @@ static dw_status check_params(const dw_solver_params* p) {
   DW_CHECK(p != nullptr, DW_ERR_ARG, "params is NULL");
   DW_CHECK(p->tol > 0 && p->tol < 1, DW_ERR_ARG, "tol %g must lie in (0, 1)", p->tol);
   DW_CHECK(p->maxiter > 0, DW_ERR_ARG, "maxiter must be positive");
-  DW_CHECK(p->inner >= DW_F64 && p->inner <= DW_DF64, DW_ERR_PRECISION, "unknown inner precision");
+  DW_CHECK(p->inner >= DW_F64 && p->inner <= DW_I16, DW_ERR_PRECISION, "unknown inner precision");
   DW_CHECK(p->outer == DW_F64 || p->outer == DW_DF64, DW_ERR_PRECISION, "outer precision must be DW_F64 or DW_DF64");
   DW_CHECK(p->inner == DW_F64 || p->inner == DW_DF64 || (p->delta >= 0 && p->delta < 1), DW_ERR_ARG,
            "delta %g must lie in [0, 1) (0: chosen by inner precision)",
@@ -89,7 +94,7 @@ dw_status solve_many(int n, const dw_field* const* U, const dw_field* const* b, 
     a.x = x + g;
     a.p = *p;
     if (a.p.delta <= 0.0)  // reliable-update threshold by inner precision
-      a.p.delta = (a.p.inner == DW_F16 || a.p.inner == DW_BF16) ? 0.01 : 1e-4;
+      a.p.delta = (a.p.inner == DW_F16 || a.p.inner == DW_BF16) ? 0.01 : a.p.inner == DW_I16 ? 1e-3 : 1e-4;
     if (mode == MODE_EO && !p->eo) mode = MODE_FULL;
     a.mode = mode;
     a.stats = stats ? stats + (size_t)g * nrhs : nullptr;

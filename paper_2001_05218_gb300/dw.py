@@ -28,9 +28,9 @@ DW_OK, DW_ERR_ARG, DW_ERR_SHAPE, DW_ERR_PRECISION, DW_ERR_OOM, DW_ERR_CUDA, \
     DW_ERR_NOT_CONVERGED, DW_ERR_BREAKDOWN, DW_ERR_TIMEOUT = range(9)
 STATUS_NAMES = ["DW_OK", "DW_ERR_ARG", "DW_ERR_SHAPE", "DW_ERR_PRECISION", "DW_ERR_OOM", "DW_ERR_CUDA",
                 "DW_ERR_NOT_CONVERGED", "DW_ERR_BREAKDOWN", "DW_ERR_TIMEOUT"]
-DW_F64, DW_F32, DW_F16, DW_BF16, DW_DF64 = range(5)
+DW_F64, DW_F32, DW_F16, DW_BF16, DW_DF64, DW_I16 = range(6)
 DW_GAUGE, DW_SPINOR_FULL, DW_SPINOR_EVEN, DW_SPINOR_ODD = range(4)
-PREC = {"f64": DW_F64, "f32": DW_F32, "f16": DW_F16, "bf16": DW_BF16, "df64": DW_DF64}
+PREC = {"f64": DW_F64, "f32": DW_F32, "f16": DW_F16, "bf16": DW_BF16, "df64": DW_DF64, "i16": DW_I16}
 
 
 class dw_lattice(ctypes.Structure):

@@ -7,7 +7,8 @@ pipes) is held to the FP64 bar;
 16-bit storage (FP16 / BF16 operands, spin projection rounded to 16 bits, FP32
 accumulation) is held to bounds derived from the unit roundoff of the storage
 type (2^-11 for FP16 values scaled to [-1, 1] per site, 2^-8 for BF16) times
-the few roundings on the path.
+the few roundings on the path; 16-bit fixed point (I16) to 2e-4 (half a unit
+of 1/32767 of the site maximum on input, links and output, FP32 arithmetic).
 Lattices are chosen so that half volumes span several thread blocks and end
 in a partial block (192, 960 and 1620 sites per parity with 128-site blocks).
 """
@@ -20,7 +21,7 @@ from paper_2001_05218_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "df64": 1e-13, "f32": 1e-6, "f16": 4e-3, "bf16": 3e-2}
+TOL = {"f64": 1e-13, "df64": 1e-13, "f32": 1e-6, "f16": 4e-3, "bf16": 3e-2, "i16": 2e-4}
 DIMS = [(4, 4, 4, 6), (8, 6, 4, 10), (6, 10, 6, 6)]
 
 
@@ -54,7 +55,7 @@ def test_apply_full_f64(dw, dims, anti_t):
 
 @pytest.mark.parametrize("dims", DIMS[:2])
 @pytest.mark.parametrize("prec,c12", [("f64", 0), ("f64", 1), ("df64", 0), ("df64", 1), ("f32", 0), ("f32", 1),
-                                      ("f16", 0), ("f16", 1), ("bf16", 0), ("bf16", 1)])
+                                      ("f16", 0), ("f16", 1), ("bf16", 0), ("bf16", 1), ("i16", 0), ("i16", 1)])
 def test_apply_precisions(dw, dims, prec, c12):
     kappa = 0.118
     U, psi = _setup(dims, 7)
@@ -71,7 +72,7 @@ def test_apply_precisions(dw, dims, prec, c12):
 
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("parity", [0, 1])
-@pytest.mark.parametrize("prec", ["f64", "df64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "i16"])
 def test_apply_schur(dw, dims, parity, prec):
     kappa = 0.125
     U, psi = _setup(dims, 17)

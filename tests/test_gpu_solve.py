@@ -44,7 +44,8 @@ def test_small_workload_full_lattice_fp64(dw):
 
 @pytest.mark.parametrize("inner,c12,outer", [("f64", 0, "f64"), ("df64", 0, "f64"), ("f32", 0, "f64"),
                                             ("f32", 1, "df64"), ("f16", 1, "f64"), ("f16", 1, "df64"),
-                                            ("bf16", 1, "df64"), ("f16", 0, "f64")])
+                                            ("bf16", 1, "df64"), ("f16", 0, "f64"), ("i16", 1, "df64"),
+                                            ("i16", 0, "f64")])
 @pytest.mark.parametrize("eo", [1, 0])
 def test_mixed_solves_reach_fp64_residual(dw, inner, c12, outer, eo):
     dims, kappa = (8, 8, 8, 8), 0.122
