@@ -81,14 +81,18 @@ def test_medium_workload_eo_mixed_and_fp64(dw):
         assert d < 1e-7
 
 
-def test_multi_rhs_point_sources(dw):
+MIXED = {"f32": dict(inner="f32"), "i16": dict(inner="i16", compress12=1, outer="df64")}
+
+
+@pytest.mark.parametrize("inner", ["f32", "i16"])
+def test_multi_rhs_point_sources(dw, inner):
     dims, kappa = (8, 8, 8, 16), 0.12
     U = I.gauge_field(dims, "exp", 8, 1, 0.4)
     srcs = np.stack([I.point_source(dims, s_, c_) for s_ in range(4) for c_ in range(3)])
     Ug = dw.gauge(dims, kappa, U)
     bg = dw.spinor(dims, srcs, nrhs=12)
     x = dw.spinor(dims, nrhs=12)
-    s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner="f32"))
+    s, st = dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, **MIXED[inner]))
     assert s == dw.DW_OK
     xs = x.download()
     for r in range(12):
@@ -96,7 +100,8 @@ def test_multi_rhs_point_sources(dw):
         assert _resid(dims, kappa, U, xs[r], srcs[r]) <= 1e-10
 
 
-def test_ragged_batch_of_lattices(dw):
+@pytest.mark.parametrize("inner", ["f32", "i16"])
+def test_ragged_batch_of_lattices(dw, inner):
     systems = [((4, 4, 4, 4), 0.115), ((8, 4, 4, 8), 0.12), ((6, 6, 6, 6), 0.125), ((4, 4, 8, 8), 0.118)]
     Us, bs, xs, host = [], [], [], []
     for i, (dims, kappa) in enumerate(systems):
@@ -106,7 +111,7 @@ def test_ragged_batch_of_lattices(dw):
         bs.append(dw.spinor(dims, b))
         xs.append(dw.spinor(dims))
         host.append((dims, kappa, U, b))
-    s, st = dw.cg_solve_batched(Us, bs, xs, dw.params(tol=1e-10, inner="f32"))
+    s, st = dw.cg_solve_batched(Us, bs, xs, dw.params(tol=1e-10, **MIXED[inner]))
     assert s == dw.DW_OK
     for i, (dims, kappa, U, b) in enumerate(host):
         assert st[i]["true_rel_resid"] <= 1e-10
