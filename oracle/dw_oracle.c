@@ -19,7 +19,7 @@
  *     antiperiodic in time (a sign -1 on every link that crosses t=L_t-1 -> 0).
  *   - Fig. 1 caption: the per-site data are 3x3 complex link matrices U and
  *     12-component complex vectors psi (4 spins x 3 colours).
- *   - Sec. 3.1.1: the CG driver owns solution, residual and search vectors and
+ *   - Sec. 3.1.1: the host-side CG loop owns solution, residual and search vectors and
  *     evaluates the stopping criterion on the full residual vector.
  *
  * Layout (canonical, host): site index  s = x + Lx*(y + Ly*(z + Lz*t));
