@@ -76,11 +76,12 @@ def _expm_ah(T):
     return (v * np.exp(1j * w)[None, :]) @ v.conj().T
 
 
-@pytest.mark.parametrize("dims,inner", [((4, 4, 4, 4), "f64"), ((8, 8, 8, 8), "f64"), ((4, 4, 4, 4), "f32")])
+@pytest.mark.parametrize("dims,inner", [((4, 4, 4, 4), "f64"), ((8, 8, 8, 8), "f64"), ((4, 4, 4, 4), "f32"),
+                                        ((4, 4, 4, 4), "f16")])
 def test_su3_force_finite_differences(env, dims, inner):
     """dS/deps along U -> exp(eps T) U at a few links, FP64 central differences
     of GPU solves, against Re tr(P^dag T) from the GPU su(3) force (the force
-    itself from a mixed-precision adjoint when inner = f32)."""
+    itself from a mixed-precision adjoint when inner = f32 or f16)."""
     torch, dw, _ = env
     kappa = 0.12
     U = I.gauge_field(dims, "exp", 63, 1, 0.4)

@@ -13,7 +13,7 @@ from paper_2001_05218_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "f32": 1e-6}
+TOL = {"f64": 1e-13, "f32": 1e-6, "df64": 1e-13, "f16": 1e-6, "i16": 1e-6}  # same kernels: equal up to rounding order
 
 
 @pytest.fixture(scope="module")
@@ -24,7 +24,7 @@ def dw():
     return m
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32", "df64", "f16", "i16"])
 @pytest.mark.parametrize("dagger", [0, 1])
 def test_noalloc_matches_dw_apply_on_two_calls(dw, prec, dagger):
     dims, kappa = (8, 6, 4, 10), 0.1234
