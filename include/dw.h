@@ -1,7 +1,7 @@
 /*
  * dw.h -- C ABI of the GB300 (sm_103a) Wilson-Dirac conjugate-gradient library.
  *
- * The problem (Korcyl & Korcyl, SoftwareX, Sec. 1 and Sec. 3.3): solve the
+ * The problem (Korcyl & Korcyl, SoftwareX, Sec. 1 and Sec. 3.2): solve the
  * large sparse linear system whose matrix is the Dirac-Wilson operator by
  * conjugate gradient, with most of the work in a low-precision data type and
  * occasional high-precision corrections (Sec. 2).  The operator, on an

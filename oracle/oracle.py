@@ -51,6 +51,8 @@ def lib():
             ("or_schur", [P, I, D, P, P, P, I, I], None),
             ("or_cgnr", [P, I, D, P, P, P, D, I, P], I),
             ("or_cg_normal", [P, I, D, P, P, P, D, I, P], I),
+            ("or_laplace", [P, I, D, P, P, P], None),
+            ("or_cg_laplace", [P, I, D, P, P, P, D, I, P], I),
             ("or_dense_dirac", [P, I, D, P, P], None),
             ("or_force", [P, I, D, P, P, P], None),
             ("or_su3_project", [ctypes.c_long, P, P, P], None),
@@ -139,6 +141,25 @@ def cg_normal(dims, kappa, U, b, tol=1e-12, maxiter=100000, anti_t=1):
     x = np.zeros_like(b)
     rr = ctypes.c_double(0)
     it = lib().or_cg_normal(_dims(dims), anti_t, kappa, pu, pb, x.ctypes.data, tol, maxiter, ctypes.byref(rr))
+    return x, it, rr.value
+
+
+def laplace(dims, kappa, U, psi, anti_t=1):
+    """Gauge-covariant Laplacian in hopping form, psi - kappa * K psi (spin-diagonal)."""
+    U, pu = _c(U)
+    psi, pp = _c(psi)
+    out = np.empty_like(psi)
+    lib().or_laplace(_dims(dims), anti_t, kappa, pu, pp, out.ctypes.data)
+    return out
+
+
+def cg_laplace(dims, kappa, U, b, tol=1e-12, maxiter=100000, anti_t=1):
+    """x = M^{-1} b for the Laplacian M by plain CG; returns (x, iters, rel_resid)."""
+    U, pu = _c(U)
+    b, pb = _c(b)
+    x = np.zeros_like(b)
+    rr = ctypes.c_double(0)
+    it = lib().or_cg_laplace(_dims(dims), anti_t, kappa, pu, pb, x.ctypes.data, tol, maxiter, ctypes.byref(rr))
     return x, it, rr.value
 
 

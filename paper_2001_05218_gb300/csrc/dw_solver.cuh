@@ -1,7 +1,7 @@
 // dw_solver.cuh -- conjugate gradient on the GPU, mixed precision with
 // high-precision reliable updates.
 //
-// The paper (Sec. 2, Sec. 3.3) runs most CG iterations in a low-precision
+// The paper (Sec. 2, Sec. 3.2) runs most CG iterations in a low-precision
 // type and corrects "for a possible bias" in high precision now and then.
 // Here the correction is the reliable update of Sleijpen & van der Vorst
 // (1996): the low-precision recursion runs until its residual has fallen by
