@@ -156,6 +156,17 @@ dw_status dw_apply_dag(const dw_field* U, const dw_field* in, dw_field* out, dw_
 /* out = D^dag D in, or Dhat^dag Dhat in for parity fields. */
 dw_status dw_normal_apply(const dw_field* U, const dw_field* in, dw_field* out, dw_stream_t stream);
 
+/* A second stencil on the same fields: the gauge-covariant Laplacian in
+ * hopping form, M = 1 - kappa K with
+ *   K(x,y) = sum_mu [ eta U_mu(x) delta_{x+mu,y} + eta U_mu(x-mu)^dag delta_{x-mu,y} ]
+ * acting on every spin component alike (eta: the boundary sign).  With
+ * kappa = 1/(8 + m^2), M = (-Delta_U + m^2)/(8 + m^2); M is Hermitian, and
+ * positive definite for kappa < 1/8.  The paper presents its CG as a backbone
+ * for other stencil operators (Sec. 1, Fig. 1 caption, Sec. 3.2); this is one.
+ * out = M in (FULL) or the Schur complement 1 - kappa^2 K_pq K_qp on parity
+ * fields, as dw_apply.  Storage FP64, FP32, FP16 or double-float. */
+dw_status dw_laplace_apply(const dw_field* U, const dw_field* in, dw_field* out, dw_stream_t stream);
+
 /* dw_apply (dagger == 0) or dw_apply_dag (dagger != 0) without allocating any
  * device memory.  The paper has no counterpart: this is for callers that
  * cannot allocate GPU memory when they call -- code sharing the GPU with a
@@ -250,6 +261,16 @@ dw_status dw_cg_solve_batched(int n, const dw_field* const* U, const dw_field* c
  * sites; used for differentiation.  Same argument rules as dw_cg_solve. */
 dw_status dw_cg_solve_normal(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
                              dw_solver_stats* stats, dw_stream_t stream);
+
+/* M x = b for the covariant Laplacian M of dw_laplace_apply: plain CG (no
+ * normal equations: M is Hermitian positive definite; kappa < 1/8 required)
+ * on the even-site Schur complement, then the odd sites, with the same
+ * reliable updates and the same final IEEE-FP64 residual |b - M x| / |b| as
+ * dw_cg_solve.  p->eo and p->verify_normal are ignored.  Inner precision:
+ * DW_F64, DW_F32 with compress12 = 0, or DW_F16 with compress12 = 1 (other
+ * choices return DW_ERR_PRECISION). */
+dw_status dw_cg_solve_laplace(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
+                              dw_solver_stats* stats, dw_stream_t stream);
 
 /* Gradients of the two differentiable forms (PyTorch convention for complex
  * numbers: for a real loss L, grad z = dL/dRe z + i dL/dIm z).

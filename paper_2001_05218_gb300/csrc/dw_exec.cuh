@@ -81,7 +81,7 @@ SolveCacheEntry* solve_cache_find(const std::vector<unsigned long long>& key);
 // synchronising the device).  The returned pointer stays valid until the next insert.
 SolveCacheEntry* solve_cache_insert(SolveCacheEntry&& e);
 
-template <int SPA, int LP, bool C12, bool DAG, class In, class Epi>
+template <int SPA, int LP, bool C12, bool DAG, int OP = OP_WILSON, class In, class Epi>
 inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int fin = FIN_STORE0) {
   Profiler& pr = profiler();
   cudaEvent_t ea = nullptr, eb = nullptr;
@@ -91,8 +91,8 @@ inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int 
     eb = pr.event();
     cudaEventRecord(ea, E.st);
   }
-  k_hop<SPA, LP, C12, DAG, In, Epi><<<E.grid(par_mode), E.P.block, 0, E.st>>>(E.P.B, par_mode, link_slot, in, epi,
-                                                                              E.ra(fin));
+  k_hop<SPA, LP, C12, DAG, In, Epi, OP><<<E.grid(par_mode), E.P.block, 0, E.st>>>(E.P.B, par_mode, link_slot, in,
+                                                                                  epi, E.ra(fin));
   if (pr.timing) {
     cudaEventRecord(eb, E.st);
     const int npar = par_mode == 2 ? 2 : 1;
@@ -103,13 +103,15 @@ inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int 
       sites += v * E.P.nrhs;
     }
     char nm[64];
-    snprintf(nm, sizeof nm, "hop %s/%s%s", prec_name(SPA), prec_name(LP), C12 ? "-c12" : "");
+    snprintf(nm, sizeof nm, "%s %s/%s%s", OP == OP_LAPLACE ? "laplace" : "hop", prec_name(SPA), prec_name(LP),
+             C12 ? "-c12" : "");
     Profiler::Rec r;
     r.cat = pr.category(nm);
     r.a = ea;
     r.b = eb;
     r.bytes = bytes;
-    r.flops = 1320.0 * sites;
+    // Wilson: 8 x (12 projection + 2 x 66 mat-vec) + 7 x 24; Laplacian: 8 x 4 x 66 + 7 x 24
+    r.flops = (OP == OP_LAPLACE ? 2280.0 : 1320.0) * sites;
     pr.recs.push_back(r);
   }
 }

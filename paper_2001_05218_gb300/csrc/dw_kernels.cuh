@@ -23,6 +23,10 @@
 namespace dw {
 
 enum Coef { C_ONE = 0, C_MK, C_PK, C_MK2, C_PK2 };
+// Stencil operator: the Wilson hopping term H, or the spin-diagonal covariant
+// hopping term K = sum_mu [U_mu(x) delta_{x+mu} + U_mu(x-mu)^dag delta_{x-mu}]
+// of the Laplacian 1 - kappa K (Hermitian: no dagger form).
+enum Op { OP_WILSON = 0, OP_LAPLACE = 1 };
 enum Gate { G_ACTIVE = 0, G_REL, G_ALL, G_XZERO, G_ZSRC };
 
 template <int C>
@@ -487,6 +491,34 @@ struct EpiXpay {
   }
 };
 
+// out = x + c*acc with the reduction Re <x, out> (the CG's p^dag A p for a
+// Hermitian operator, x = p).
+template <int SPO, int SPX, int COEF>
+struct EpiXpayDot {
+  static constexpr bool kReduce = true;
+  int slot_out, slot_x;
+  int gate;
+  __host__ double io_bytes() const { return Spin<SPX>::kBytes + Spin<SPO>::kBytes; }
+  template <typename R>
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12], double& nrm) const {
+    using RO = typename Spin<SPO>::R;
+    Cx<typename Spin<SPX>::R> xv[12];
+    Spin<SPX>::load(slot_ptr(S, slot_x, r, par), S.vh, s, xv);
+    const R c = (R)coef_of<COEF>(S.kappa);
+    Cx<RO> o[12];
+    R n = (R)0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const R xr = (R)xv[k].re, xi = (R)xv[k].im;
+      const R re = fma(c, acc[k].re, xr), im = fma(c, acc[k].im, xi);
+      o[k] = cx((RO)re, (RO)im);
+      n = fma(xr, re, fma(xi, im, n));
+    }
+    nrm = (double)n;
+    Spin<SPO>::store(slot_wptr(S, slot_out, r, par), S.vh, s, o);
+  }
+};
+
 // Reliable update on the even-odd system, in the high precision SPH, at even site s:
 //   x <- x + xl;  xl <- 0;  r_hi = bh - x + kappa^2 * acc  (acc = H_eo t_hi);
 //   r_low <- r_hi;  reduction |r_hi|^2.
@@ -601,6 +633,70 @@ struct EpiResidFull {
     reduce_finalize(S, T, RB, tt, ntiles, val, ra);                        \
   }
 
+// ------------------------------------------------------------------ the Laplacian's directions
+// acc = K psi at output site s: the neighbour's whole spinor (no projection)
+// times U_mu(x) or U_mu(x-mu)^dag, spin by spin, with the boundary sign.
+template <int SPA, int LP, bool C12, class In, typename R>
+__device__ __forceinline__ void laplace_dirs(const SysDesc& S, const In& in, const Coord& c, int s, int r, int pin,
+                                             const char* ulink_own, const char* ulink_nb, long long mu_stride,
+                                             Cx<R> (&acc)[12]) {
+#pragma unroll 1
+  for (int d = 0; d < 8; ++d) {
+    const int mu = d >> 1;
+    const bool fwd = (d & 1) == 0;
+    float eta;
+    const int n = neighbour_rt(S, c, s, mu, fwd ? +1 : -1, &eta);
+    const char* lb = (fwd ? ulink_own : ulink_nb) + mu * mu_stride;
+    const int li = fwd ? s : n;
+    if constexpr (SPA == P16 || SPA == PB16) {
+      uint32_t pw[12], h0[6], h1[6], u[9];
+      float sc;
+      Cx<float> g0[6], g1[6];
+      in.load_words(S, pin, r, n, pw, sc);
+      Link<LP, C12>::load_words(lb, S.vh, li, u);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        h0[k] = pw[k];
+        h1[k] = pw[6 + k];
+      }
+      if (fwd) {
+        su3_mul_w<false, SPA>(u, h0, g0);
+        su3_mul_w<false, SPA>(u, h1, g1);
+      } else {
+        su3_mul_w<true, SPA>(u, h0, g0);
+        su3_mul_w<true, SPA>(u, h1, g1);
+      }
+      const float w = eta < 0.f ? -sc : sc;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        acc[k] = cfma(w, g0[k], acc[k]);
+        acc[6 + k] = cfma(w, g1[k], acc[6 + k]);
+      }
+    } else {
+      Cx<R> p[12], h0[6], h1[6], g0[6], g1[6], u[9];
+      in.load(S, pin, r, n, p);
+      Link<LP, C12>::load(lb, S.vh, li, u);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        h0[k] = eta < 0.f ? cx(-p[k].re, -p[k].im) : p[k];
+        h1[k] = eta < 0.f ? cx(-p[6 + k].re, -p[6 + k].im) : p[6 + k];
+      }
+      if (fwd) {
+        su3_mul<false>(u, h0, g0);
+        su3_mul<false>(u, h1, g1);
+      } else {
+        su3_mul<true>(u, h0, g0);
+        su3_mul<true>(u, h1, g1);
+      }
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        acc[k] = acc[k] + g0[k];
+        acc[6 + k] = acc[6 + k] + g1[k];
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ the stencil kernel
 // par_mode 0/1: output parity fixed, grid = ntot blocks.  par_mode 2: both
 // parities, grid = 2*ntot (block b >= ntot works on odd output sites).
@@ -621,7 +717,7 @@ struct HopOccupancy {
   static constexpr int kMinBlocks = (SPA == P16 || SPA == PB16) ? DW_HOP16_MINB : SPA == PDF ? DW_HOPDF_MINB : 1;
 };
 
-template <int SPA, int LP, bool C12, bool DAG, class In, class Epi>
+template <int SPA, int LP, bool C12, bool DAG, class In, class Epi, int OP = OP_WILSON>
 __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
     k_hop(const __grid_constant__ Batch B, int par_mode, int link_slot, In in, Epi epi, RedArgs ra) {
   using R = typename Spin<SPA>::R;
@@ -675,6 +771,13 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
     su3_mul_w<true, SPA>(u, h, g);                                              \
     accumulate_w<MU, SB>(acc, g, eta < 0.f ? -sc : sc);                         \
   }
+    if constexpr (OP == OP_LAPLACE) {
+      laplace_dirs<SPA, LP, C12>(S, in, c, s, r, pin, ulink_own, ulink_nb, mu_stride, acc);
+      if constexpr (SPA == PDF) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) acc[k] = cx(renorm(acc[k].re), renorm(acc[k].im));
+      }
+    } else
 #ifndef DW_HOP16_CONVERT
     if constexpr (SPA == P16 || SPA == PB16) {
       DW_HOP_DIR_W(0)

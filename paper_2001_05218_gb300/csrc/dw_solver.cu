@@ -25,6 +25,23 @@ DW_CG_EXTERN(PI16, P32, true, P64)
 DW_CG_EXTERN(PI16, P32, false, PDF)
 DW_CG_EXTERN(PI16, P32, true, PDF)
 #undef DW_CG_EXTERN
+#define DW_CG_LAP_EXTERN(L, A, C, H) extern template struct CG<L, A, C, H, OP_LAPLACE>;
+DW_CG_LAP_EXTERN(P64, P64, false, P64)
+DW_CG_LAP_EXTERN(P32, P32, false, P64)
+DW_CG_LAP_EXTERN(P32, P32, false, PDF)
+DW_CG_LAP_EXTERN(P16, P32, true, P64)
+DW_CG_LAP_EXTERN(P16, P32, true, PDF)
+#undef DW_CG_LAP_EXTERN
+
+// The covariant Laplacian (MODE_HERM): inner FP64, FP32 with 18-real links or
+// FP16 with 12-real links.
+template <int H>
+static dw_status dispatch_laplace_inner(const SolveArgs& a) {
+  if (a.p.inner == DW_F32 && !a.p.compress12) return CG<P32, P32, false, H, OP_LAPLACE>::run(a);
+  if (a.p.inner == DW_F16 && a.p.compress12) return CG<P16, P32, true, H, OP_LAPLACE>::run(a);
+  return set_error(DW_ERR_PRECISION,
+                   "the Laplacian solver runs inner FP64, FP32 with 18-real links or FP16 with 12-real links");
+}
 
 template <int H>
 static dw_status dispatch_inner(const SolveArgs& a) {
@@ -40,6 +57,10 @@ static dw_status dispatch_inner(const SolveArgs& a) {
 }
 
 static dw_status dispatch(const SolveArgs& a) {
+  if (a.mode == MODE_HERM) {
+    if (a.p.inner == DW_F64) return CG<P64, P64, false, P64, OP_LAPLACE>::run(a);
+    return a.p.outer == DW_DF64 ? dispatch_laplace_inner<PDF>(a) : dispatch_laplace_inner<P64>(a);
+  }
   if (a.p.inner == DW_F64) return CG<P64, P64, false, P64>::run(a);
   if (a.p.inner == DW_DF64) return CG<PDF, PDF, false, PDF>::run(a);
   return a.p.outer == DW_DF64 ? dispatch_inner<PDF>(a) : dispatch_inner<P64>(a);
@@ -143,6 +164,11 @@ dw_status dw_cg_solve_batched(int n, const dw_field* const* U, const dw_field* c
 dw_status dw_cg_solve_normal(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
                              dw_solver_stats* stats, dw_stream_t stream) {
   return solve_many(1, &U, &b, &x, p, stats, reinterpret_cast<cudaStream_t>(stream), MODE_NORMAL);
+}
+
+dw_status dw_cg_solve_laplace(const dw_field* U, const dw_field* b, dw_field* x, const dw_solver_params* p,
+                              dw_solver_stats* stats, dw_stream_t stream) {
+  return solve_many(1, &U, &b, &x, p, stats, reinterpret_cast<cudaStream_t>(stream), MODE_HERM);
 }
 
 }  // extern "C"

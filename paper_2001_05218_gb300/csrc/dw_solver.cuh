@@ -23,6 +23,10 @@
 //               Source b_e + k H_eo b_o; after convergence x_o = b_o + k H_oe x_e.
 //   MODE_FULL   CGNR on the full lattice (D = 1 - k H).
 //   MODE_NORMAL plain CG on D^dag D x = b (z = r, w = D^dag D p, |Dp|^2 = p.Ap).
+//   MODE_HERM   plain CG on the even-site Schur complement of a Hermitian
+//               positive definite operator 1 - k K (the covariant Laplacian,
+//               OP_LAPLACE): z = r, w = Mhat p, alpha = |r|^2 / Re(p.w);
+//               source, reconstruction and certification as in MODE_EO.
 // Every CG scalar is formed on the device in FP64 by the finalizer of the
 // reduction that produces it; the host only polls an "active columns" count.
 #pragma once
@@ -34,7 +38,9 @@
 
 namespace dw {
 
-enum Mode { MODE_EO = 0, MODE_FULL = 1, MODE_NORMAL = 2 };
+enum Mode { MODE_EO = 0, MODE_FULL = 1, MODE_NORMAL = 2, MODE_HERM = 3 };
+// modes whose CG vectors live on the even sites only
+inline bool eo_mode(int mode) { return mode == MODE_EO || mode == MODE_HERM; }
 
 struct SolveArgs {
   int n;
@@ -57,53 +63,62 @@ static __global__ void k_set_deadline(ColState* cols, int n, unsigned long long 
   if (i < n && budget_ns) cols[i].deadline_ns = globaltimer_ns() + budget_ns;
 }
 
-template <int L, int A, bool C12, int H>
+template <int L, int A, bool C12, int H, int OP = OP_WILSON>
 struct CG {
   static constexpr int kLinkHi = S_LHI;
   static constexpr int kLinkLo = S_LLO;
 
   // reliable update (gated by do_rel) and its finalizer
   static void reliable(const Exec& E, int mode) {
-    if (mode == MODE_EO) {
-      hop<H, H, false, false>(E, 1, kLinkHi, InSum<H, A>{S_X, S_XL}, EpiOut<H, C_ONE>{S_RT, G_REL});
-      hop<H, H, false, false>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiReliableEO<L, A, H>{G_REL}, FIN_RELIABLE);
+    if constexpr (OP == OP_LAPLACE) {  // MODE_HERM: r = bh - x + k^2 K_eo K_oe x, as MODE_EO
+      hop<H, H, false, false, OP>(E, 1, kLinkHi, InSum<H, A>{S_X, S_XL}, EpiOut<H, C_ONE>{S_RT, G_REL});
+      hop<H, H, false, false, OP>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiReliableEO<L, A, H>{G_REL}, FIN_RELIABLE);
+    } else if (mode == MODE_EO) {
+      hop<H, H, false, false, OP>(E, 1, kLinkHi, InSum<H, A>{S_X, S_XL}, EpiOut<H, C_ONE>{S_RT, G_REL});
+      hop<H, H, false, false, OP>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiReliableEO<L, A, H>{G_REL}, FIN_RELIABLE);
     } else if (mode == MODE_FULL) {
       count_launch();
       k_fold_x<A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
-      hop<H, H, false, false>(E, 2, kLinkHi, InOne<H>{S_X}, EpiResidFull<L, true, H>{G_REL, S_RT, S_X, S_B},
+      hop<H, H, false, false, OP>(E, 2, kLinkHi, InOne<H>{S_X}, EpiResidFull<L, true, H>{G_REL, S_RT, S_X, S_B},
                               FIN_RELIABLE);
     } else {
       count_launch();
       k_fold_x<A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
       // t = D x ; r = b - D^dag t
-      hop<H, H, false, false>(E, 2, kLinkHi, InOne<H>{S_X}, EpiXpay<H, H, C_MK, false>{S_AUX0, S_X, G_REL});
-      hop<H, H, false, true>(E, 2, kLinkHi, InOne<H>{S_AUX0}, EpiResidFull<L, true, H>{G_REL, S_RT, S_AUX0, S_B},
+      hop<H, H, false, false, OP>(E, 2, kLinkHi, InOne<H>{S_X}, EpiXpay<H, H, C_MK, false>{S_AUX0, S_X, G_REL});
+      hop<H, H, false, true, OP>(E, 2, kLinkHi, InOne<H>{S_AUX0}, EpiResidFull<L, true, H>{G_REL, S_RT, S_AUX0, S_B},
                              FIN_RELIABLE);
     }
   }
 
   // z = A-side residual and its norm with finalizer fin (FIN_GAMMA0 / FIN_BETA)
   static void zstep(const Exec& E, int mode, int fin) {
-    if (mode == MODE_EO) {
-      hop<L, L, C12, true>(E, 1, kLinkLo, InOne<L>{S_R}, EpiOut<L, C_ONE>{S_T, G_ACTIVE});
-      hop<L, L, C12, true>(E, 0, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK2, true>{S_Z, S_R, G_ACTIVE}, fin);
+    if constexpr (OP == OP_LAPLACE) {
+      norm<L>(E, 0, S_R, fin);  // MODE_HERM: z aliases r
+    } else if (mode == MODE_EO) {
+      hop<L, L, C12, true, OP>(E, 1, kLinkLo, InOne<L>{S_R}, EpiOut<L, C_ONE>{S_T, G_ACTIVE});
+      hop<L, L, C12, true, OP>(E, 0, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK2, true>{S_Z, S_R, G_ACTIVE}, fin);
     } else if (mode == MODE_FULL) {
-      hop<L, L, C12, true>(E, 2, kLinkLo, InOne<L>{S_R}, EpiXpay<L, L, C_MK, true>{S_Z, S_R, G_ACTIVE}, fin);
+      hop<L, L, C12, true, OP>(E, 2, kLinkLo, InOne<L>{S_R}, EpiXpay<L, L, C_MK, true>{S_Z, S_R, G_ACTIVE}, fin);
     } else {
       norm<L>(E, 2, S_R, fin);  // z aliases r
     }
   }
 
   static void wstep(const Exec& E, int mode) {
-    if (mode == MODE_EO) {
-      hop<L, L, C12, false>(E, 1, kLinkLo, InOne<L>{S_P}, EpiOut<L, C_ONE>{S_T, G_ACTIVE});
-      hop<L, L, C12, false>(E, 0, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK2, true>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
+    if constexpr (OP == OP_LAPLACE) {
+      // MODE_HERM: w = Mhat p = p - k^2 K_eo K_oe p and p^dag w
+      hop<L, L, C12, false, OP>(E, 1, kLinkLo, InOne<L>{S_P}, EpiOut<L, C_ONE>{S_T, G_ACTIVE});
+      hop<L, L, C12, false, OP>(E, 0, kLinkLo, InOne<L>{S_T}, EpiXpayDot<L, L, C_MK2>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
+    } else if (mode == MODE_EO) {
+      hop<L, L, C12, false, OP>(E, 1, kLinkLo, InOne<L>{S_P}, EpiOut<L, C_ONE>{S_T, G_ACTIVE});
+      hop<L, L, C12, false, OP>(E, 0, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK2, true>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
     } else if (mode == MODE_FULL) {
-      hop<L, L, C12, false>(E, 2, kLinkLo, InOne<L>{S_P}, EpiXpay<L, L, C_MK, true>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
+      hop<L, L, C12, false, OP>(E, 2, kLinkLo, InOne<L>{S_P}, EpiXpay<L, L, C_MK, true>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
     } else {
       // t = D p (|t|^2 = p^dag A p);  w = D^dag t
-      hop<L, L, C12, false>(E, 2, kLinkLo, InOne<L>{S_P}, EpiXpay<L, L, C_MK, true>{S_T, S_P, G_ACTIVE}, FIN_ALPHA);
-      hop<L, L, C12, true>(E, 2, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK, false>{S_W, S_T, G_ACTIVE});
+      hop<L, L, C12, false, OP>(E, 2, kLinkLo, InOne<L>{S_P}, EpiXpay<L, L, C_MK, true>{S_T, S_P, G_ACTIVE}, FIN_ALPHA);
+      hop<L, L, C12, true, OP>(E, 2, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK, false>{S_W, S_T, G_ACTIVE});
     }
   }
 
@@ -137,11 +152,11 @@ struct CaptureStreams {
 // reliable update in an if-node }.  Both conditions are set on the device,
 // the loop is capped at maxiter + 2 passes, and every column also leaves the
 // loop through its own maxiter / timeout / breakdown checks.
-template <int L, int A, bool C12, int H>
-dw_status CG<L, A, C12, H>::build_graph(const Exec& E0, int mode, cudaGraphExec_t* exec, int* body_kernels,
+template <int L, int A, bool C12, int H, int OP>
+dw_status CG<L, A, C12, H, OP>::build_graph(const Exec& E0, int mode, cudaGraphExec_t* exec, int* body_kernels,
                                         int* rel_kernels) {
   static thread_local CaptureStreams cs;
-  const int pm = mode == MODE_EO ? 0 : 2;
+  const int pm = eo_mode(mode) ? 0 : 2;
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   DW_CUDA(cudaGraphCreate(&g, 0));
@@ -226,11 +241,11 @@ dw_status CG<L, A, C12, H>::build_graph(const Exec& E0, int mode, cudaGraphExec_
 // Host-stepped loop: identical kernels, the host reads the device counters
 // after every update so that no launch is made without work; used while the
 // launch profiler is active.
-template <int L, int A, bool C12, int H>
-dw_status CG<L, A, C12, H>::run_stepped(const Exec& E, int mode, int maxiter) {
+template <int L, int A, bool C12, int H, int OP>
+dw_status CG<L, A, C12, H, OP>::run_stepped(const Exec& E, int mode, int maxiter) {
   static Flags* hf = nullptr;
   if (!hf) DW_CUDA(cudaMallocHost((void**)&hf, sizeof(Flags)));
-  const int pm = mode == MODE_EO ? 0 : 2;
+  const int pm = eo_mode(mode) ? 0 : 2;
   for (int it = 0; it < maxiter + 2; ++it) {
     DW_CUDA(cudaMemcpyAsync(hf, E.rb.flags, sizeof(Flags), cudaMemcpyDeviceToHost, E.st));
     DW_CUDA(cudaStreamSynchronize(E.st));
@@ -251,12 +266,12 @@ dw_status CG<L, A, C12, H>::run_stepped(const Exec& E, int mode, int maxiter) {
 }
 
 
-template <int L, int A, bool C12, int H>
-dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
+template <int L, int A, bool C12, int H, int OP>
+dw_status CG<L, A, C12, H, OP>::run(const SolveArgs& a) {
   const int n = a.n;
   const int mode = a.mode;
   const int nrhs = a.b[0]->nrhs;
-  const bool eo = mode == MODE_EO;
+  const bool eo = eo_mode(mode);
   const int fpar = eo ? 1 : 2;  // parities held by the inner vectors
   cudaStream_t st = a.st;
 
@@ -270,7 +285,8 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
     DW_TRY(derived_links(a.U[i], L, C12 ? 1 : 0, st, &lo_links[i]));
     DW_TRY(derived_links(a.U[i], H, 0, st, &hi_links[i]));
   }
-  std::vector<unsigned long long> key = {0xC6ull, (unsigned long long)L, (unsigned long long)A, C12 ? 1ull : 0ull,
+  std::vector<unsigned long long> key = {0xC6ull, (unsigned long long)OP, (unsigned long long)L, (unsigned long long)A,
+                                         C12 ? 1ull : 0ull,
                                          (unsigned long long)H, (unsigned long long)mode, (unsigned long long)nrhs,
                                          (unsigned long long)a.p.tile, (unsigned long long)a.p.verify_normal,
                                          (unsigned long long)n};
@@ -345,7 +361,7 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
       S.f[S_X] = S.f[S_XU];
       for (size_t k = 0; k < pieces.size(); ++k)
         S.f[pieces[k].slot] = arena_slot(fresh.arena + poff[i][k], lats[i], pieces[k].prec, nrhs, pieces[k].npar);
-      if (mode == MODE_NORMAL) S.f[S_Z] = S.f[S_R];
+      if (mode == MODE_NORMAL || mode == MODE_HERM) S.f[S_Z] = S.f[S_R];
       for (auto pc : {S_XL, S_P})
         fresh.zero.push_back({S.f[pc].p, (size_t)nrhs * fpar * (pc == S_XL ? spin_bytes(A) : spin_bytes(L)) * S.vh});
     }
@@ -403,7 +419,7 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
   for (auto& z : ent->zero) DW_CUDA(cudaMemsetAsync(z.first, 0, z.second, st));
   if (eo) {
     // bh = b_e + kappa H_eo b_o
-    hop<H, H, false, false>(E, 0, kLinkHi, InOne<H>{S_B}, EpiXpay<H, H, C_PK, false>{S_BH, S_B, G_ALL});
+    hop<H, H, false, false, OP>(E, 0, kLinkHi, InOne<H>{S_B}, EpiXpay<H, H, C_PK, false>{S_BH, S_B, G_ALL});
   }
   // zero guess: r = source (bh or b); otherwise r = source - A x, recomputed
   count_launch();
@@ -435,7 +451,7 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
 
   // ---- finish: odd sites, then the IEEE FP64 residual from the caller's fields
   if (eo) {
-    hop<H, H, false, false>(E, 1, kLinkHi, InOne<H>{S_X}, EpiXpay<H, H, C_PK, false>{S_X, S_B, G_ALL});
+    hop<H, H, false, false, OP>(E, 1, kLinkHi, InOne<H>{S_X}, EpiXpay<H, H, C_PK, false>{S_X, S_B, G_ALL});
   }
   if (H != P64) {
     count_launch();
@@ -445,21 +461,26 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
   k_zero_zsrc<P64><<<E.grid(2), E.P.block, 0, st>>>(E.P.B, 2, S_XU, E.ra(FIN_STORE0));  // zero source: x = 0
   const int rt64 = H == P64 ? S_RT : S_AUX1;  // FP64 full temporary (verify_normal)
   if (mode != MODE_NORMAL) {
-    hop<P64, P64, false, false>(E, 2, S_LF64, InOne<P64>{S_XU},
+    hop<P64, P64, false, false, OP>(E, 2, S_LF64, InOne<P64>{S_XU},
                                 EpiResidFull<L, false, P64>{G_ALL, a.p.verify_normal ? rt64 : -1, S_XU, S_BU},
                                 FIN_STORE0);
-    if (a.p.verify_normal) {
-      hop<P64, P64, false, true>(E, 2, S_LF64, InOne<P64>{rt64}, EpiXpay<P64, P64, C_MK, true>{-1, rt64, G_ALL},
-                                 FIN_STORE1);
-      hop<P64, P64, false, true>(E, 2, S_LF64, InOne<P64>{S_BU}, EpiXpay<P64, P64, C_MK, true>{-1, S_BU, G_ALL},
-                                 FIN_STORE2);
+    if constexpr (OP == OP_WILSON) {
+      if (a.p.verify_normal) {
+        hop<P64, P64, false, true, OP>(E, 2, S_LF64, InOne<P64>{rt64}, EpiXpay<P64, P64, C_MK, true>{-1, rt64, G_ALL},
+                                       FIN_STORE1);
+        hop<P64, P64, false, true, OP>(E, 2, S_LF64, InOne<P64>{S_BU}, EpiXpay<P64, P64, C_MK, true>{-1, S_BU, G_ALL},
+                                       FIN_STORE2);
+      }
     }
   } else {
-    // |b - D^dag D x|^2 in FP64: t = D x into the FP64 temporary, then b - D^dag t
-    const int t64 = H == P64 ? S_AUX0 : S_AUX1;
-    hop<P64, P64, false, false>(E, 2, S_LF64, InOne<P64>{S_XU}, EpiXpay<P64, P64, C_MK, false>{t64, S_XU, G_ALL});
-    hop<P64, P64, false, true>(E, 2, S_LF64, InOne<P64>{t64}, EpiResidFull<L, false, P64>{G_ALL, -1, t64, S_BU},
-                               FIN_STORE0);
+    if constexpr (OP == OP_WILSON) {
+      // |b - D^dag D x|^2 in FP64: t = D x into the FP64 temporary, then b - D^dag t
+      const int t64 = H == P64 ? S_AUX0 : S_AUX1;
+      hop<P64, P64, false, false, OP>(E, 2, S_LF64, InOne<P64>{S_XU},
+                                      EpiXpay<P64, P64, C_MK, false>{t64, S_XU, G_ALL});
+      hop<P64, P64, false, true, OP>(E, 2, S_LF64, InOne<P64>{t64}, EpiResidFull<L, false, P64>{G_ALL, -1, t64, S_BU},
+                                     FIN_STORE0);
+    }
   }
   DW_CUDA(cudaEventRecord(ev1, st));
   DW_CUDA(cudaMemcpyAsync(hc.data(), E.rb.cols, sizeof(ColState) * hc.size(), cudaMemcpyDeviceToHost, st));
@@ -489,7 +510,8 @@ dw_status CG<L, A, C12, H>::run(const SolveArgs& a) {
         o.iters = c.iter;
         o.reliable_updates = c.nrel > 0 ? c.nrel - 1 : 0;
         o.true_rel_resid = true_rel;
-        o.normal_rel_resid = mode == MODE_NORMAL ? true_rel
+        o.normal_rel_resid = mode == MODE_HERM     ? -1.0
+                             : mode == MODE_NORMAL ? true_rel
                              : a.p.verify_normal ? sqrt(c.store[1] / (c.store[2] > 0 ? c.store[2] : 1.0))
                                                  : -1.0;
         o.time_ms = ms;

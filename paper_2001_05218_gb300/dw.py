@@ -82,6 +82,8 @@ _SIGS = {
     "dw_cg_solve_batched": [_I, ctypes.POINTER(_FP), ctypes.POINTER(_FP), ctypes.POINTER(_FP),
                             ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_solver_stats), _P],
     "dw_cg_solve_normal": [_FP, _FP, _FP, ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_solver_stats), _P],
+    "dw_cg_solve_laplace": [_FP, _FP, _FP, ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_solver_stats), _P],
+    "dw_laplace_apply": [_FP, _FP, _FP, _P],
     "dw_profile_start": [_I],
     "dw_profile_stop": [ctypes.POINTER(dw_profile_entry), _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_longlong)],
     "dw_cg_backward": [_FP, _FP, _FP, _FP, _FP, _FP, _I, ctypes.POINTER(dw_solver_params),
@@ -254,6 +256,22 @@ def cg_solve_normal(U: Field, b: Field, x: Field, p: dw_solver_params = None, ra
     p = p or params()
     st = (dw_solver_stats * b.nrhs)()
     s = dw_cg_solve_normal(U.handle, b.handle, x.handle, ctypes.byref(p), st, current_stream())
+    if raise_on_fail:
+        check(s)
+    return s, [st[i].as_dict() for i in range(b.nrhs)]
+
+
+def laplace_apply(U: Field, x: Field, out: Field):
+    """out = M x for the covariant Laplacian M = 1 - kappa K (Schur complement on parity fields)."""
+    check(dw_laplace_apply(U.handle, x.handle, out.handle, current_stream()))
+    return out
+
+
+def cg_solve_laplace(U: Field, b: Field, x: Field, p: dw_solver_params = None, raise_on_fail=True):
+    """M x = b for the covariant Laplacian by plain CG (see dw_cg_solve_laplace)."""
+    p = p or params()
+    st = (dw_solver_stats * b.nrhs)()
+    s = dw_cg_solve_laplace(U.handle, b.handle, x.handle, ctypes.byref(p), st, current_stream())
     if raise_on_fail:
         check(s)
     return s, [st[i].as_dict() for i in range(b.nrhs)]
