@@ -250,16 +250,18 @@ def run_dslash(args):
     y = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=prec, nrhs=args.nrhs)
     l2 = torch.cuda.get_device_properties(0).L2_cache_size
     scratch = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
+    op = dw.laplace_apply if args.op == "laplace" else dw.apply
     for _ in range(max(1, args.warmup)):
-        dw.apply(Ug, x, y)
+        op(Ug, x, y)
     torch.cuda.synchronize()
     dw.profile_start(time_stencils=True)
     for _ in range(args.steps):
         scratch.fill_(1)
-        dw.apply(Ug, x, y)
+        op(Ug, x, y)
     prof, launches = dw.profile_stop()
     peak, kind = peaks()
-    out = {"mode": "dslash", "workload": args.workload, "prec": args.dslash, "compress12": c12, "nrhs": args.nrhs,
+    out = {"mode": "dslash", "op": args.op, "workload": args.workload, "prec": args.dslash, "compress12": c12,
+           "nrhs": args.nrhs,
            "kernels": {}}
     for k, e in prof.items():
         pl = e["total_ms"] / e["launches"]
@@ -327,6 +329,21 @@ def run_suite(args):
         # (not even-odd) CGNR, whose operator uses every link twice per launch
         ("f32_mixed_12real_links", dict(MIX32, compress12=1)), ("i16_mixed", MIXI16),
         ("f64_full_lattice", dict(F64, eo=0)), ("f16_mixed_full_lattice", dict(MIX16, eo=0))])
+    # the second stencil (covariant Laplacian) on the same links and sources
+    def single_laplace(name, configs):
+        dims, kappa, U, b = I.make_workload(name)
+        Ug, bg, xg = dw.gauge(dims, kappa, U), dw.spinor(dims, b), dw.spinor(dims)
+        res = {}
+        for label, kw in configs:
+            p = dw.params(**kw)
+            ms, (s, stt) = timed(lambda: (zero(xg), dw.cg_solve_laplace(Ug, bg, xg, p))[1])
+            res[label] = {"ms": ms, "iters": stt[0]["iters"], "reliable_updates": stt[0]["reliable_updates"],
+                          "true_rel_resid": stt[0]["true_rel_resid"]}
+        return res
+
+    LAP = [("f64", F64), ("f32_mixed", MIX32), ("f16_mixed", MIX16)]
+    out["laplace_16x16x16x32_exp0.4"] = single_laplace("wilson_16x16x16x32_exp0.4", LAP)
+    out["laplace_32x32x32x64_exp0.6"] = single_laplace("wilson_32x32x32x64_exp0.6", LAP[1:])
     out["wilson_32x32x32x64_exp0.6"] = single("wilson_32x32x32x64_exp0.6", [
         ("f16_mixed_eo", MIX16), ("f16_mixed_full_lattice", dict(MIX16, eo=0)),
         ("f32_mixed_eo", MIX32), ("f32_mixed_12real_links", dict(MIX32, compress12=1)), ("i16_mixed_eo", MIXI16)])
@@ -402,6 +419,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dslash", default=None, help="stencil-only mode: f64|f32|f16|bf16|i16|df64 (Schur operator applies)")
     ap.add_argument("--nrhs", type=int, default=1, help="stencil-only mode: right-hand sides per field")
+    ap.add_argument("--op", default="wilson", choices=["wilson", "laplace"],
+                    help="stencil-only mode: the Wilson operator or the covariant Laplacian")
     ap.add_argument("--suite", action="store_true", help="time every workload configuration (not the benchmark line)")
     args = ap.parse_args()
     if args.impl == "reference":
