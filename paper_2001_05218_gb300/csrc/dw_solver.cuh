@@ -17,7 +17,7 @@
 // that certifies the solve is always recomputed in IEEE FP64 from the
 // caller's x, b and links.
 //
-// Three systems share the machinery (A = operator, r = b - A x tracked):
+// Four systems share the machinery (A = operator, r = b - A x tracked):
 //   MODE_EO     CGNR on the even-site Schur complement Dhat = 1 - k^2 H_eo H_oe:
 //               z = Dhat^dag r, w = Dhat p, alpha = |z|^2/|w|^2, beta = |z'|^2/|z|^2.
 //               Source b_e + k H_eo b_o; after convergence x_o = b_o + k H_oe x_e.
