@@ -590,20 +590,26 @@ def main():
         # whole job: the slowest rank's median step, as for the device-timed value
         e2e_value, e2e_ms = aggregate_throughput(float(np.median(wall)) * 1e3, 1, world, "cuda")
         e2e_s = e2e_ms / 1e3
-        # one more step with events between the phases (stream time)
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
-        evs[0].record(stream)
-        dw.check(dw.dw_field_upload(Ug.handle, ctypes.c_void_p(Uh.data_ptr()), sp))
-        evs[1].record(stream)
-        dw.check(dw.dw_field_upload(bg.handle, ctypes.c_void_p(bh.data_ptr()), sp))
-        evs[2].record(stream)
-        reset_x()
-        dw.cg_solve(Ug, bg, xg, p_mix)
-        evs[3].record(stream)
-        dw.check(dw.dw_field_download(xg.handle, ctypes.c_void_p(xh.data_ptr()), sp))
-        evs[4].record(stream)
-        torch.cuda.synchronize()
-        phases = {k: evs[i].elapsed_time(evs[i + 1]) for i, k in enumerate(["upload_U", "upload_b", "solve", "download_x"])}
+        # three more steps with events between the phases (stream time); the
+        # median of each phase is reported
+        names = ["upload_U", "upload_b", "solve", "download_x"]
+        samples = {k: [] for k in names}
+        for _ in range(3):
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            evs[0].record(stream)
+            dw.check(dw.dw_field_upload(Ug.handle, ctypes.c_void_p(Uh.data_ptr()), sp))
+            evs[1].record(stream)
+            dw.check(dw.dw_field_upload(bg.handle, ctypes.c_void_p(bh.data_ptr()), sp))
+            evs[2].record(stream)
+            reset_x()
+            dw.cg_solve(Ug, bg, xg, p_mix)
+            evs[3].record(stream)
+            dw.check(dw.dw_field_download(xg.handle, ctypes.c_void_p(xh.data_ptr()), sp))
+            evs[4].record(stream)
+            torch.cuda.synchronize()
+            for i, k in enumerate(names):
+                samples[k].append(evs[i].elapsed_time(evs[i + 1]))
+        phases = {k: float(np.median(v)) for k, v in samples.items()}
         e2e = {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(Uh.numel() * 8 + bh.numel() * 8),
                "d2h_bytes_per_step": int(xh.numel() * 8), "ms_per_step": e2e_s * 1e3, "statistic": "median",
                "steps": ne, "mean_ms_per_step": float(np.mean(wall)) * 1e3,
