@@ -101,7 +101,8 @@ typedef struct dw_field dw_field; /* opaque handle */
  * 16-bit spinors store 24 halves plus one FP32 scale per site; 16-bit links
  * store the link entries directly (|U_ij| <= 1).  compress12 applies to
  * gauge fields: only rows 0 and 1 are stored and row 2 is rebuilt as
- * conj(row0 x row1), valid for SU(3) links. */
+ * conj(row0 x row1), valid for SU(3) links.  nrhs: right-hand sides held by
+ * a spinor field, 1..64 (gauge fields: 1); others return DW_ERR_SHAPE. */
 dw_status dw_field_bytes(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs,
                          size_t* bytes);
 

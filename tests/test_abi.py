@@ -59,3 +59,18 @@ def test_params_default_and_null_checks(dw):
 
 def test_binding_has_same_names_as_header(dw):
     assert set(header_functions()) <= set(dw.symbols())
+
+
+def test_field_bytes_rhs_range_and_fixed_point(dw):
+    """nrhs spans 1..64 (per-block column gates are sized for 64); the
+    fixed-point format has the 16-bit layout (52 bytes per spinor site,
+    24 per 12-real link)."""
+    nb = ctypes.c_size_t()
+    lat = dw.lattice((4, 4, 4, 4), 0.1)
+    assert dw.dw_field_bytes(ctypes.byref(lat), dw.DW_SPINOR_FULL, dw.DW_F16, 0, 64, ctypes.byref(nb)) == dw.DW_OK
+    assert nb.value == 64 * 256 * 52
+    assert dw.dw_field_bytes(ctypes.byref(lat), dw.DW_SPINOR_FULL, dw.DW_F16, 0, 65, ctypes.byref(nb)) == dw.DW_ERR_SHAPE
+    assert dw.dw_field_bytes(ctypes.byref(lat), dw.DW_SPINOR_EVEN, dw.DW_I16, 0, 2, ctypes.byref(nb)) == dw.DW_OK
+    assert nb.value == 2 * 128 * 52
+    assert dw.dw_field_bytes(ctypes.byref(lat), dw.DW_GAUGE, dw.DW_I16, 1, 1, ctypes.byref(nb)) == dw.DW_OK
+    assert nb.value == 256 * 4 * 24
