@@ -1,9 +1,11 @@
-"""Writes tests/golden/dirac_2x2x2x4.txt from the FP64 oracle alone.
+"""Writes tests/golden/dirac_2x2x2x4.txt and laplace_2x2x2x4.txt from the
+FP64 oracle alone.
 
-The paper prints no worked example, so this fixture is a regression pin of the
-oracle (and a fixed target for the GPU path): a seeded Haar gauge field and a
-seeded Gaussian source on a 2x2x2x4 lattice (antiperiodic time, kappa 0.12),
-with D psi, D^dag psi and the CGNR solution x = D^{-1} psi at every site.
+The paper prints no worked example, so these fixtures are regression pins of
+the oracle (and fixed targets for the GPU path): a seeded Haar gauge field and
+a seeded Gaussian source on a 2x2x2x4 lattice (antiperiodic time, kappa 0.12),
+with D psi, D^dag psi and the CGNR solution x = D^{-1} psi at every site, and,
+for the covariant Laplacian M, M psi and x = M^{-1} psi by plain CG.
 Run:  python tests/golden/make_golden.py
 """
 import os
@@ -41,5 +43,24 @@ def main():
                         Ddag[s, sp, c].real, Ddag[s, sp, c].imag, x[s, sp, c].real, x[s, sp, c].imag))
 
 
+def main_laplace():
+    U = I.gauge_field(DIMS, "haar", SEED, 1)
+    psi = I.gaussian_spinor(DIMS, SEED, 2)
+    Mpsi = O.laplace(DIMS, KAPPA, U, psi)
+    x, it, rr = O.cg_laplace(DIMS, KAPPA, U, psi, tol=1e-14)
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "laplace_2x2x2x4.txt")
+    with open(path, "w") as f:
+        f.write("# M psi and x = M^{-1} psi for the covariant Laplacian M = 1 - kappa K, FP64 oracle (make_golden.py)\n")
+        f.write("# dims %s kappa %.17g seed %d antiperiodic_t 1 cg_iters %d rel_resid %.3e\n"
+                % (" ".join(map(str, DIMS)), KAPPA, SEED, it, rr))
+        f.write("# columns: site spin colour re(Mpsi) im(Mpsi) re(x) im(x)\n")
+        for s in range(I.volume(DIMS)):
+            for sp in range(4):
+                for c in range(3):
+                    f.write("%d %d %d %.17e %.17e %.17e %.17e\n" % (
+                        s, sp, c, Mpsi[s, sp, c].real, Mpsi[s, sp, c].imag, x[s, sp, c].real, x[s, sp, c].imag))
+
+
 if __name__ == "__main__":
     main()
+    main_laplace()

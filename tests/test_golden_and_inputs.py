@@ -69,3 +69,30 @@ def test_generator_is_counter_based_and_gaussian():
     psi = I.gaussian_spinor((8, 8, 8, 8), 5, 2)
     assert psi.shape == (4096, 4, 3)
     assert abs(np.mean(psi.real ** 2) - 1) < 0.05 and abs(np.mean(psi.imag ** 2) - 1) < 0.05
+
+
+GOLDEN_LAPLACE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "laplace_2x2x2x4.txt")
+
+
+def load_golden_laplace():
+    meta = {}
+    with open(GOLDEN_LAPLACE) as f:
+        for line in f:
+            if line.startswith("# dims"):
+                tok = line[2:].split()
+                meta["dims"] = tuple(int(v) for v in tok[1:5])
+                meta["kappa"] = float(tok[6])
+                meta["seed"] = int(tok[8])
+    rows = np.loadtxt(GOLDEN_LAPLACE)
+    V = I.volume(meta["dims"])
+    cols = rows[:, 3:].reshape(V, 4, 3, 4)
+    return meta, cols[..., 0] + 1j * cols[..., 1], cols[..., 2] + 1j * cols[..., 3]
+
+
+def test_oracle_reproduces_laplace_golden():
+    meta, Mpsi, x = load_golden_laplace()
+    dims, kappa, seed = meta["dims"], meta["kappa"], meta["seed"]
+    U = I.gauge_field(dims, "haar", seed, 1)
+    psi = I.gaussian_spinor(dims, seed, 2)
+    assert np.abs(O.laplace(dims, kappa, U, psi) - Mpsi).max() < 1e-13
+    assert np.linalg.norm(O.laplace(dims, kappa, U, x) - psi) / np.linalg.norm(psi) < 1e-13

@@ -87,3 +87,19 @@ def test_laplace_multi_rhs_and_bad_precision(dw):
         assert np.linalg.norm(O.laplace(dims, kappa, U, xs[r]) - bs[r]) / np.linalg.norm(bs[r]) <= 1e-10
     s, _ = dw.cg_solve_laplace(Ug, bg, xg, dw.params(tol=1e-10, inner="bf16", compress12=1), raise_on_fail=False)
     assert s == dw.DW_ERR_PRECISION
+
+
+def test_laplace_golden_fixture_on_gpu(dw):
+    """The committed oracle fixture (extent-2 directions: forward and backward
+    neighbours coincide) through dw_laplace_apply and dw_cg_solve_laplace."""
+    from test_golden_and_inputs import load_golden_laplace
+    meta, Mpsi, x = load_golden_laplace()
+    dims, kappa, seed = meta["dims"], meta["kappa"], meta["seed"]
+    U = I.gauge_field(dims, "haar", seed, 1)
+    psi = I.gaussian_spinor(dims, seed, 2)
+    Ug, pg, out = dw.gauge(dims, kappa, U), dw.spinor(dims, psi), dw.spinor(dims)
+    dw.laplace_apply(Ug, pg, out)
+    assert site_err(out.download(), Mpsi) <= 1e-13
+    xg = dw.spinor(dims)
+    s, st = dw.cg_solve_laplace(Ug, pg, xg, dw.params(tol=1e-12, inner="f64"))
+    assert s == dw.DW_OK and np.linalg.norm(xg.download() - x) / np.linalg.norm(x) <= 1e-10
