@@ -521,13 +521,14 @@ struct EpiXpayDot {
 
 // Reliable update on the even-odd system, in the high precision SPH, at even site s:
 //   x <- x + xl;  xl <- 0;  r_hi = bh - x + kappa^2 * acc  (acc = H_eo t_hi);
-//   r_low <- r_hi;  reduction |r_hi|^2.
+//   r_low <- r_hi;  reduction |r_hi|^2.  r_hi itself is not stored: the
+//   iteration continues from r_low, and the next correction recomputes r_hi.
 template <int SPL, int SPA, int SPH>
 struct EpiReliableEO {
   static constexpr bool kReduce = true;
   int gate;
   __host__ double io_bytes() const {
-    return 4.0 * Spin<SPH>::kBytes + 2.0 * Spin<SPA>::kBytes + Spin<SPL>::kBytes;
+    return 3.0 * Spin<SPH>::kBytes + 2.0 * Spin<SPA>::kBytes + Spin<SPL>::kBytes;
   }
   template <typename RH>
   __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<RH> (&acc)[12],
@@ -551,7 +552,6 @@ struct EpiReliableEO {
     nrm = (double)n;
     Spin<SPH>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
     Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, zero);
-    Spin<SPH>::store(slot_wptr(S, S_RT, r, par), S.vh, s, rv);
     Cx<typename Spin<SPL>::R> lo[12];
     convert12(rv, lo);
     Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, lo);
