@@ -145,13 +145,18 @@ class ClockSampler:
 
 
 def source_hash():
-    """Hash of the files that define the stencil kernel (storage formats and
-    the kernel template): a DRAM-traffic figure is only reported for the
-    kernel it was measured on."""
+    """Hash of the code (comments and blank lines removed) of the files that
+    define the stencil kernel (storage formats and the kernel template): a
+    DRAM-traffic figure is only reported for the kernel it was measured on."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2001_05218_gb300", "csrc")
     for f in ("dw_common.cuh", "dw_kernels.cuh"):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        text = open(os.path.join(csrc, f)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = [ln.rstrip() for ln in text.splitlines() if ln.strip()]
+        h.update("\n".join(code).encode())
     return h.hexdigest()[:16]
 
 

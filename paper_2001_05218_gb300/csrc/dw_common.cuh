@@ -1,6 +1,6 @@
 // dw_common.cuh -- device-side building blocks of the Wilson-Dirac CG library:
 // complex arithmetic, field storage formats, the batch/system descriptor and
-// the deterministic one-pass grid reduction with the CG scalar updates.
+// the deterministic two-level grid reduction with the CG scalar updates.
 //
 // Storage (per parity block of Vh sites, per right-hand side), structure of
 // arrays so that consecutive threads (consecutive even-odd site indices)
