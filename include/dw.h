@@ -111,9 +111,22 @@ dw_status dw_field_alloc(const dw_lattice* lat, dw_kind kind, dw_prec prec, int 
                          dw_field** out);
 
 /* Make a field handle over caller-owned device memory of at least
- * dw_field_bytes() bytes, 256-byte aligned (e.g. a torch tensor's storage). */
+ * dw_field_bytes() bytes, 256-byte aligned (e.g. a torch tensor's storage).
+ * The solvers keep copies of a gauge field's links in their inner and outer
+ * storage formats (FP32, FP16, double-float, ...) on the handle and refresh
+ * them only when the field has changed through the library (upload, import)
+ * or through dw_field_mark_modified: a caller that rewrites a wrapped gauge
+ * field's memory itself must call dw_field_mark_modified before the next
+ * solve, or that solve runs on the old links (and fails its FP64
+ * certification, which always reads the caller's memory). */
 dw_status dw_field_wrap(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs,
                         void* dev_ptr, size_t bytes, dw_field** out);
+
+/* Declare that the field's device memory was changed outside the library
+ * (e.g. a wrapped tensor written in place): derived copies of its links are
+ * rebuilt, on the solver's stream, by the next call that needs them.  Cheap;
+ * enqueues nothing. */
+dw_status dw_field_mark_modified(dw_field* f);
 
 /* Release a handle (and its memory if it was made by dw_field_alloc).
  * Waits for the device to finish work that may use it. */
@@ -156,6 +169,17 @@ dw_status dw_apply_dag(const dw_field* U, const dw_field* in, dw_field* out, dw_
 
 /* out = D^dag D in, or Dhat^dag Dhat in for parity fields. */
 dw_status dw_normal_apply(const dw_field* U, const dw_field* in, dw_field* out, dw_stream_t stream);
+
+/* out = D in (dagger == 0) or D^dag in (dagger != 0), as dw_apply, and
+ * norm2[r] = |out_r|^2 for every right-hand side r, summed in FP64 by the
+ * library's deterministic two-level grid reduction inside the launch that
+ * writes out -- the same fused epilogue (xpay plus squared norm) that forms
+ * w = Dhat p and |w|^2 in every CG iteration (the per-iteration matrix-vector
+ * product and residual norm of the paper's Sec. 3.1 and Sec. 3.1.1).  The squared norm is taken of
+ * the output before it is rounded to the storage precision.  norm2: host
+ * array of out->nrhs doubles.  Synchronises `stream` before returning. */
+dw_status dw_apply_norm(const dw_field* U, const dw_field* in, dw_field* out, int dagger, double* norm2,
+                        dw_stream_t stream);
 
 /* A second stencil on the same fields: the gauge-covariant Laplacian in
  * hopping form, M = 1 - kappa K with

@@ -8,6 +8,7 @@ grad z = dL/dRe z + i dL/dIm z.
   CGSolve.apply(U, b, lattice, params)        x = (D^dag D)^{-1} b
   PseudofermionAction.apply(U, phi, lattice, params)
                                               S = phi^dag (D^dag D)^{-1} phi
+                                                = |D (D^dag D)^{-1} phi|^2
 Every solve and the link force run in the library's kernels; this module
 moves tensors in and out of fields.
 """
@@ -75,7 +76,10 @@ class PseudofermionAction(torch.autograd.Function):
         xf = dw.Field(lat, dw.DW_SPINOR_FULL)
         dw.cg_solve_normal(Uf, pf, xf, p)
         X = xf.export()
-        S = torch.vdot(phi.reshape(-1), X.reshape(-1)).real
+        # S = phi^dag X = X^dag D^dag D X = |D X|^2, from the library's FP64
+        # grid reduction fused into the launch that applies D to X
+        yf = dw.Field(lat, dw.DW_SPINOR_FULL)
+        S = torch.tensor(float(dw.apply_norm(Uf, xf, yf)[0]), dtype=torch.float64, device=phi.device)
         ctx.save_for_backward(U, phi, X if not p.recompute_fwd else torch.empty(0))
         ctx.lat, ctx.p, ctx.su3 = lat, p, su3_project
         return S

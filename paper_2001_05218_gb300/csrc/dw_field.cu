@@ -115,19 +115,25 @@ void geometry(SysDesc& S, const dw_lattice& l, int nrhs) {
   S.kappa = l.kappa;
 }
 
-void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T, int RB) {
-  memset(&P.B, 0, sizeof P.B);
-  P.nsys = (int)lats.size();
-  P.nrhs = nrhs;
-  if (T <= 0 || RB <= 0) {  // defaults: 128 sites per block, or 64 x (a divisor of nrhs up to 4)
-    RB = 1;
-    T = 128;
-    if (nrhs > 1) {
-      T = 64;
-      for (int d = 4; d >= 1; --d)
-        if (nrhs % d == 0) { RB = d; break; }
-    }
+void default_block_shape(int nrhs, int* T, int* RB) {
+  // 128 sites per block, or 64 sites x (the largest divisor of nrhs up to 4)
+  *RB = 1;
+  *T = 128;
+  if (nrhs > 1) {
+    *T = 64;
+    for (int d = 4; d >= 1; --d)
+      if (nrhs % d == 0) {
+        *RB = d;
+        break;
+      }
   }
+}
+
+void make_plan(Plan& P, const dw_lattice* lats, int n, int nrhs, int T, int RB) {
+  memset(&P.B, 0, sizeof P.B);
+  P.nsys = n;
+  P.nrhs = nrhs;
+  if (T <= 0 || RB <= 0) default_block_shape(nrhs, &T, &RB);
   P.B.nsys = P.nsys;
   P.B.T = T;
   P.B.RB = RB;
@@ -423,6 +429,21 @@ static void tune_load_once() {
     if (T >= 32 && T <= 256 && T % 32 == 0 && RB >= 1 && T * RB <= 256) tune_table()[key] = BlockShape{T, RB};
   fclose(f);
 }
+std::string tune_key(const dw_lattice* lats, int n, int nrhs, int prec, int c12) {
+  char dev_name[256] = "gpu";
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
+    snprintf(dev_name, sizeof dev_name, "%s", prop.name);
+  for (char* c = dev_name; *c; ++c)
+    if (*c == ' ') *c = '_';
+  std::string key = std::string(dev_name) + "/v3/" + prec_name(prec) + (c12 ? "c12" : "c18") + "/r" +
+                    std::to_string(nrhs);
+  for (int i = 0; i < n; ++i)
+    key += "/" + std::to_string(lats[i].dims[0]) + "x" + std::to_string(lats[i].dims[1]) + "x" +
+           std::to_string(lats[i].dims[2]) + "x" + std::to_string(lats[i].dims[3]);
+  return key;
+}
 bool tune_lookup(const std::string& key, BlockShape* out) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   tune_load_once();
@@ -587,6 +608,12 @@ dw_status dw_field_alloc(const dw_lattice* lat, dw_kind kind, dw_prec prec, int 
 dw_status dw_field_wrap(const dw_lattice* lat, dw_kind kind, dw_prec prec, int compress12, int nrhs, void* dev_ptr,
                         size_t bytes, dw_field** out) {
   return make_field(lat, kind, prec, compress12, nrhs, dev_ptr, bytes, 0, out);
+}
+
+dw_status dw_field_mark_modified(dw_field* f) {
+  DW_CHECK(f != nullptr, DW_ERR_ARG, "field is NULL");
+  f->version += 1;
+  return DW_OK;
 }
 
 dw_status dw_field_free(dw_field* f) {

@@ -19,7 +19,7 @@ struct dw_field {
   size_t bytes;
   int owned;
   int device;
-  unsigned long long version;  // bumped by every upload/import
+  unsigned long long version;  // bumped by every upload/import and by dw_field_mark_modified
   // gauge fields: cached copies in other storage formats (solver inner links)
   struct Derived {
     int prec, c12;
@@ -81,8 +81,13 @@ struct Plan {
   dim3 block, grid1, grid2;  // one parity / both parities
 };
 // T sites per block and RB right-hand sides per block (T*RB <= 256, T a
-// multiple of 32); T <= 0 or RB <= 0 selects the defaults.
-void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T, int RB = 0);
+// multiple of 32); T <= 0 or RB <= 0 selects the defaults.  Allocates nothing.
+void make_plan(Plan& P, const dw_lattice* lats, int n, int nrhs, int T, int RB = 0);
+inline void make_plan(Plan& P, const std::vector<dw_lattice>& lats, int nrhs, int T, int RB = 0) {
+  make_plan(P, lats.data(), (int)lats.size(), nrhs, T, RB);
+}
+// The default block shape for nrhs right-hand sides.
+void default_block_shape(int nrhs, int* T, int* RB);
 
 // Autotuned block shape (T, RB) for the inner stencil of a batch, cached per
 // (lattices, nrhs, storage, link compression, device) in memory and in the
@@ -92,6 +97,8 @@ struct BlockShape {
 };
 bool tune_lookup(const std::string& key, BlockShape* out);
 void tune_store(const std::string& key, BlockShape v);
+// Key of the tuning cache: device name, storage, nrhs and every lattice.
+std::string tune_key(const dw_lattice* lats, int n, int nrhs, int prec, int c12);
 
 // Device scratch for reductions of one plan.
 struct RedBuf {

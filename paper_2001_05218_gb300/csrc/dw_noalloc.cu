@@ -18,6 +18,9 @@
 // name is only a stand-in, not a device address), so the device address is
 // looked up once per device with cudaGetSymbolAddress, by the first call made
 // with that device current.  Make that first call before any stream capture.
+// The address is kept for the life of the process: after cudaDeviceReset the
+// array lives at a new address in the new context, so a process that resets a
+// device must not call this function on that device again.
 #include <mutex>
 
 #include "dw_exec.cuh"
@@ -79,33 +82,16 @@ extern "C" dw_status dw_apply_noalloc(const dw_field* U, const dw_field* in, dw_
   void* scratch = nullptr;
   if (need > 0) DW_TRY(scratch_address(&scratch));
 
-  // single-system launch plan, built without heap allocation
+  // single-system launch plan with the default block shape (the plan builder
+  // allocates nothing)
   Exec E;
   E.st = reinterpret_cast<cudaStream_t>(stream);
-  memset(&E.P.B, 0, sizeof E.P.B);
-  const int nrhs = in->nrhs;
-  int T = 128, RB = 1;
-  if (nrhs > 1) {
-    T = 64;
-    for (int d = 4; d >= 1; --d)
-      if (nrhs % d == 0) { RB = d; break; }
-  }
+  make_plan(E.P, &U->lat, 1, in->nrhs, 0, 0);
   SysDesc& S = E.P.B.sd[0];
-  geometry(S, U->lat, nrhs);
-  S.tpp = (S.vh + T - 1) / T;
-  E.P.nsys = E.P.B.nsys = 1;
-  E.P.nrhs = nrhs;
-  E.P.ncols = nrhs;
-  E.P.B.T = T;
-  E.P.B.RB = RB;
-  E.P.B.ntot = S.tpp;
-  E.P.block = dim3(T * RB);
-  E.P.grid1 = dim3(S.tpp, (nrhs + RB - 1) / RB);
-  E.P.grid2 = dim3(2 * S.tpp, (nrhs + RB - 1) / RB);
   S.f[S_LLO] = gauge_slot(U->ptr, U->lat, U->prec, U->compress12);
   S.f[S_AUX0] = spinor_slot(in);
   S.f[S_AUX2] = spinor_slot(out);
-  if (scratch) S.f[S_AUX1] = arena_slot(static_cast<char*>(scratch), in->lat, in->prec, nrhs, 1);
+  if (scratch) S.f[S_AUX1] = arena_slot(static_cast<char*>(scratch), in->lat, in->prec, in->nrhs, 1);
 
   const int c12 = U->compress12;
 #define DW_NOALLOC_CASE(PP)                                \

@@ -1,25 +1,9 @@
 // dw_ops.cu -- dw_apply, dw_apply_dag, dw_normal_apply.
-//
-// Full lattice: out = in - kappa * H in, one launch over both parities.
-// Parity p (Schur complement, q = 1 - p):
-//   tmp_q = H_qp in_p ;  out_p = in_p - kappa^2 H_pq tmp_q   (two launches).
-// The dagger uses the swapped projectors (gamma_5-conjugate operator).
-#include "dw_exec.cuh"
+#include "dw_apply.cuh"
 
 namespace dw {
 
-template <int P, bool C12, bool DAG>
-static void apply_launch(const Exec& E, dw_kind kind) {
-  if (kind == DW_SPINOR_FULL) {
-    hop<P, P, C12, DAG>(E, 2, S_LLO, InOne<P>{S_AUX0}, EpiXpay<P, P, C_MK, false>{S_AUX2, S_AUX0, G_ALL});
-  } else {
-    const int p = kind == DW_SPINOR_EVEN ? 0 : 1;
-    hop<P, P, C12, DAG>(E, 1 - p, S_LLO, InOne<P>{S_AUX0}, EpiOut<P, C_ONE>{S_AUX1, G_ALL});
-    hop<P, P, C12, DAG>(E, p, S_LLO, InOne<P>{S_AUX1}, EpiXpay<P, P, C_MK2, false>{S_AUX2, S_AUX0, G_ALL});
-  }
-}
-
-static dw_status check_op(const dw_field* U, const dw_field* in, const dw_field* out) {
+dw_status check_op(const dw_field* U, const dw_field* in, const dw_field* out) {
   DW_CHECK(U && in && out, DW_ERR_ARG, "NULL field");
   DW_CHECK(U->kind == DW_GAUGE, DW_ERR_ARG, "first argument must be a gauge field");
   DW_CHECK(in->kind != DW_GAUGE && out->kind == in->kind, DW_ERR_SHAPE, "in/out must be spinors of the same kind");
@@ -31,12 +15,17 @@ static dw_status check_op(const dw_field* U, const dw_field* in, const dw_field*
   return DW_OK;
 }
 
+void apply_plan(Plan& P, const dw_field* U, const dw_field* in) {
+  BlockShape shape{0, 0};
+  tune_lookup(tune_key(&U->lat, 1, in->nrhs, U->prec, U->compress12), &shape);
+  make_plan(P, &U->lat, 1, in->nrhs, shape.T, shape.RB);
+}
+
 // One application of D (or D^dag) with temporaries from the stream-ordered pool.
 static dw_status apply_one(const dw_field* U, const dw_field* in, dw_field* out, int dag, cudaStream_t st) {
   Exec E;
   E.st = st;
-  std::vector<dw_lattice> lats(1, U->lat);
-  make_plan(E.P, lats, in->nrhs, 0);
+  apply_plan(E.P, U, in);
   SysDesc& S = E.P.B.sd[0];
   S.f[S_LLO] = gauge_slot(U->ptr, U->lat, U->prec, U->compress12);
   S.f[S_AUX0] = spinor_slot(in);
@@ -47,28 +36,9 @@ static dw_status apply_one(const dw_field* U, const dw_field* in, dw_field* out,
     DW_CUDA(cudaMallocAsync((void**)&tmp, nb, st));
     S.f[S_AUX1] = arena_slot(tmp, in->lat, in->prec, in->nrhs, 1);
   }
-  const int c12 = U->compress12;
-#define DW_APPLY_CASE(PP)                                                      \
-  if (c12) {                                                                   \
-    if (dag) apply_launch<PP, true, true>(E, in->kind);                        \
-    else apply_launch<PP, true, false>(E, in->kind);                           \
-  } else {                                                                     \
-    if (dag) apply_launch<PP, false, true>(E, in->kind);                       \
-    else apply_launch<PP, false, false>(E, in->kind);                          \
-  }
-  switch (in->prec) {
-    case DW_F64: DW_APPLY_CASE(P64) break;
-    case DW_F32: DW_APPLY_CASE(P32) break;
-    case DW_F16: DW_APPLY_CASE(P16) break;
-    case DW_BF16: DW_APPLY_CASE(PB16) break;
-    case DW_DF64: DW_APPLY_CASE(PDF) break;
-    case DW_I16: DW_APPLY_CASE(PI16) break;
-  }
-#undef DW_APPLY_CASE
-  cudaError_t e = cudaGetLastError();
+  dw_status s = apply_dispatch<false>(E, U, in, dag);
   if (tmp) cudaFreeAsync(tmp, st);
-  DW_CUDA(e);
-  return DW_OK;
+  return s;
 }
 
 }  // namespace dw

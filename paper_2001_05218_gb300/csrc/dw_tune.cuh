@@ -16,17 +16,7 @@ namespace dw {
 template <int L, bool C12>
 BlockShape tune_inner_shape(const std::vector<dw_lattice>& lats, int nrhs, const std::vector<const char*>& links,
                             cudaStream_t st) {
-  char dev_name[256] = "gpu";
-  int dev = 0;
-  cudaDeviceProp prop;
-  if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess)
-    snprintf(dev_name, sizeof dev_name, "%s", prop.name);
-  for (char* c = dev_name; *c; ++c)
-    if (*c == ' ') *c = '_';
-  std::string key = std::string(dev_name) + "/v3/" + prec_name(L) + (C12 ? "c12" : "c18") + "/r" + std::to_string(nrhs);
-  for (auto& l : lats)
-    key += "/" + std::to_string(l.dims[0]) + "x" + std::to_string(l.dims[1]) + "x" + std::to_string(l.dims[2]) +
-           "x" + std::to_string(l.dims[3]);
+  const std::string key = tune_key(lats.data(), (int)lats.size(), nrhs, L, C12 ? 1 : 0);
   BlockShape best{0, 0};
   if (tune_lookup(key, &best)) return best;
 

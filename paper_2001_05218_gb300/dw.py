@@ -76,6 +76,8 @@ _SIGS = {
     "dw_apply": [_FP, _FP, _FP, _P],
     "dw_apply_dag": [_FP, _FP, _FP, _P],
     "dw_normal_apply": [_FP, _FP, _FP, _P],
+    "dw_apply_norm": [_FP, _FP, _FP, _I, ctypes.POINTER(ctypes.c_double), _P],
+    "dw_field_mark_modified": [_FP],
     "dw_apply_noalloc": [_FP, _FP, _FP, _I, _P],
     "dw_solver_params_default": [ctypes.POINTER(dw_solver_params)],
     "dw_cg_solve": [_FP, _FP, _FP, ctypes.POINTER(dw_solver_params), ctypes.POINTER(dw_solver_stats), _P],
@@ -210,6 +212,11 @@ class Field:
         check(dw_field_export(self.handle, ctypes.c_void_p(t.data_ptr()), stream or current_stream()))
         return t
 
+    def mark_modified(self):
+        """Declare that self.storage was written in place (dw_field_mark_modified)."""
+        check(dw_field_mark_modified(self.handle))
+        return self
+
     def free(self):
         if getattr(self, "handle", None):
             dw_field_free(self.handle)
@@ -241,6 +248,14 @@ def apply(U: Field, x: Field, out: Field, dag=False, normal=False):
     fn = dw_normal_apply if normal else (dw_apply_dag if dag else dw_apply)
     check(fn(U.handle, x.handle, out.handle, current_stream()))
     return out
+
+
+def apply_norm(U: Field, x: Field, out: Field, dag=False):
+    """out = D x (or D^dag x); returns |out_r|^2 per right-hand side from the
+    library's FP64 grid reduction (dw_apply_norm)."""
+    n = (ctypes.c_double * x.nrhs)()
+    check(dw_apply_norm(U.handle, x.handle, out.handle, 1 if dag else 0, n, current_stream()))
+    return np.array(n[:], dtype=np.float64)
 
 
 def cg_solve(U: Field, b: Field, x: Field, p: dw_solver_params = None, raise_on_fail=True):

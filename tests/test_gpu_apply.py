@@ -70,16 +70,24 @@ def test_apply_precisions(dw, dims, prec, c12):
         assert e <= TOL[prec], (prec, c12, dag, e)
 
 
+SCHUR_CASES = [("f64", 0), ("df64", 0), ("f32", 0), ("f32", 1), ("i16", 0), ("i16", 1),
+               ("f16", 0), ("f16", 1), ("bf16", 0), ("bf16", 1)]
+
+
 @pytest.mark.parametrize("dims", DIMS)
 @pytest.mark.parametrize("parity", [0, 1])
-@pytest.mark.parametrize("prec", ["f64", "df64", "f32", "i16"])
-def test_apply_schur(dw, dims, parity, prec):
+@pytest.mark.parametrize("prec,c12", SCHUR_CASES)
+def test_apply_schur(dw, dims, parity, prec, c12):
+    """The even-odd Schur complement Dhat = 1 - kappa^2 H_pq H_qp, its adjoint
+    and Dhat^dag Dhat, site by site against the oracle, in every storage
+    precision with 18- and 12-real links: the 16-bit 12-real operator is the
+    one the mixed-precision solver iterates with."""
     kappa = 0.125
     U, psi = _setup(dims, 17)
     par = parity_of_sites(dims)
     P = dw.PREC[prec]
     kind = dw.DW_SPINOR_EVEN if parity == 0 else dw.DW_SPINOR_ODD
-    Ug = dw.gauge(dims, kappa, U, prec=P)
+    Ug = dw.gauge(dims, kappa, U, prec=P, compress12=c12)
     sub = psi[par == parity]
     x = dw.spinor(dims, sub, kind=kind, prec=P)
     out = dw.spinor(dims, kind=kind, prec=P)
@@ -88,11 +96,74 @@ def test_apply_schur(dw, dims, parity, prec):
     for dag in (False, True):
         dw.apply(Ug, x, out, dag=dag)
         ref = O.schur(dims, kappa, U, full, parity=parity, dag=dag)[par == parity]
-        assert site_err(out.download(), ref) <= TOL[prec]
+        e = site_err(out.download(), ref)
+        assert e <= TOL[prec], (prec, c12, dag, e)
     dw.apply(Ug, x, out, normal=True)
     t = O.schur(dims, kappa, U, full, parity=parity)
     ref = O.schur(dims, kappa, U, t, parity=parity, dag=True)[par == parity]
     assert site_err(out.download(), ref) <= 10 * TOL[prec]
+
+
+NORM_CASES = [("f16", 1, "even"), ("f16", 1, "odd"), ("f16", 0, "even"), ("bf16", 1, "even"), ("bf16", 0, "odd"),
+              ("i16", 1, "even"), ("f32", 1, "even"), ("f32", 0, "full"), ("f16", 1, "full"), ("f64", 0, "even"),
+              ("f64", 0, "full"), ("df64", 0, "even")]
+
+
+@pytest.mark.parametrize("dims", DIMS[1:])
+@pytest.mark.parametrize("prec,c12,kind", NORM_CASES)
+def test_apply_norm_reducing_epilogue(dw, dims, prec, c12, kind):
+    """dw_apply_norm runs the solver's reducing epilogue (out = x + c H t with
+    |out|^2 reduced in FP64 over the grid): its output must match the oracle
+    site by site, and the returned |out|^2 must match |oracle|^2 to the
+    storage precision's bound (the norm is of the value before its rounding
+    to storage, so it carries the operator's error, not the store's)."""
+    kappa = 0.121
+    U, psi = _setup(dims, 19)
+    par = parity_of_sites(dims)
+    P = dw.PREC[prec]
+    k = {"even": dw.DW_SPINOR_EVEN, "odd": dw.DW_SPINOR_ODD, "full": dw.DW_SPINOR_FULL}[kind]
+    Ug = dw.gauge(dims, kappa, U, prec=P, compress12=c12)
+    if kind == "full":
+        full, keep = psi, np.ones(len(psi), dtype=bool)
+    else:
+        pty = 0 if kind == "even" else 1
+        keep = par == pty
+        full = np.where(keep[:, None, None], psi, 0)
+    x = dw.spinor(dims, full[keep], kind=k, prec=P)
+    out = dw.spinor(dims, kind=k, prec=P)
+    for dag in (False, True):
+        n2 = dw.apply_norm(Ug, x, out, dag=dag)
+        if kind == "full":
+            ref = O.dirac(dims, kappa, U, psi, dag=dag)
+        else:
+            ref = O.schur(dims, kappa, U, full, parity=pty, dag=dag)[keep]
+        e = site_err(out.download(), ref)
+        assert e <= TOL[prec], (prec, c12, kind, dag, e)
+        ref2 = float(np.vdot(ref.reshape(-1), ref.reshape(-1)).real)
+        assert abs(n2[0] - ref2) <= 2 * TOL[prec] * ref2, (n2[0], ref2)
+
+
+def test_apply_norm_multi_rhs_and_repeatability(dw):
+    """Per right-hand side norms of a 12-RHS FP16 field, and bitwise-equal
+    norms on repeated calls (fixed-order reduction)."""
+    dims, kappa, n = (8, 6, 4, 10), 0.12, 12
+    U, _ = _setup(dims, 41)
+    par = parity_of_sites(dims)
+    psis = np.stack([I.gaussian_spinor(dims, 41, 10 + r)[par == 0] * (1 + r) for r in range(n)])
+    Ug = dw.gauge(dims, kappa, U, prec=dw.DW_F16, compress12=1)
+    x = dw.spinor(dims, psis, kind=dw.DW_SPINOR_EVEN, prec=dw.DW_F16, nrhs=n)
+    out = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=dw.DW_F16, nrhs=n)
+    a = dw.apply_norm(Ug, x, out)
+    b = dw.apply_norm(Ug, x, out)
+    assert np.array_equal(a, b)
+    got = out.download()
+    for r in range(n):
+        full = np.zeros((int(np.prod(dims)), 4, 3), dtype=np.complex128)
+        full[par == 0] = psis[r]
+        ref = O.schur(dims, kappa, U, full, parity=0)[par == 0]
+        assert site_err(got[r], ref) <= TOL["f16"]
+        ref2 = float(np.vdot(ref.reshape(-1), ref.reshape(-1)).real)
+        assert abs(a[r] - ref2) <= 2 * TOL["f16"] * ref2
 
 
 def test_normal_apply_full(dw):
@@ -116,6 +187,37 @@ def test_multi_rhs_apply(dw):
     got = out.download()
     for r in range(n):
         assert site_err(got[r], O.dirac(dims, kappa, U, psis[r])) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("prec,c12", [("f16", 1), ("bf16", 1), ("f16", 0), ("i16", 1), ("f32", 1)])
+@pytest.mark.parametrize("kind", ["full", "even"])
+def test_multi_rhs_apply_12_sources(dw, prec, c12, kind):
+    """12 right-hand sides (the spin-colour sources of the multi-RHS solve) in
+    16-bit and FP32 storage with 12-real links: every column against the
+    oracle, full lattice and even-site Schur complement, both D and D^dag."""
+    dims, kappa, n = (6, 10, 6, 6), 0.12, 12
+    U, _ = _setup(dims, 43)
+    par = parity_of_sites(dims)
+    P = dw.PREC[prec]
+    psis = np.stack([I.gaussian_spinor(dims, 43, 10 + r) for r in range(n)])
+    if kind == "even":
+        psis = np.where((par == 0)[None, :, None, None], psis, 0)
+        x = dw.spinor(dims, psis[:, par == 0], kind=dw.DW_SPINOR_EVEN, prec=P, nrhs=n)
+        out = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=P, nrhs=n)
+    else:
+        x = dw.spinor(dims, psis, prec=P, nrhs=n)
+        out = dw.spinor(dims, prec=P, nrhs=n)
+    Ug = dw.gauge(dims, kappa, U, prec=P, compress12=c12)
+    for dag in (False, True):
+        dw.apply(Ug, x, out, dag=dag)
+        got = out.download()
+        for r in range(n):
+            if kind == "even":
+                ref = O.schur(dims, kappa, U, psis[r], parity=0, dag=dag)[par == 0]
+            else:
+                ref = O.dirac(dims, kappa, U, psis[r], dag=dag)
+            e = site_err(got[r], ref)
+            assert e <= TOL[prec], (prec, c12, kind, dag, r, e)
 
 
 def test_layout_roundtrip_is_exact(dw):

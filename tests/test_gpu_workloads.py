@@ -59,6 +59,34 @@ def test_bench_workload_df64_operator(dw, big):
     assert site_err(out.download(), O.dirac(dims, kappa, U, b)) <= 1e-13
 
 
+def test_bench_workload_fp16_schur_operator(dw, big):
+    """The operator the benchmark's solver iterates with, at full size: the
+    FP16 (per-site scale, 16-bit operands, FP32 accumulation) even-site Schur
+    complement with 12-real links, with the block shape the autotuner chose
+    for this lattice (a solve first tunes it), site by site against the
+    oracle, D and D^dag, and the reducing epilogue's FP64 |out|^2."""
+    from helpers import parity_of_sites
+    dims, kappa, U, b = big
+    Ug = dw.gauge(dims, kappa, U)
+    bg, xg = dw.spinor(dims, b), dw.spinor(dims)
+    s, st = dw.cg_solve(Ug, bg, xg, dw.params(tol=1e-10, inner="f16", compress12=1, outer="df64"))
+    assert s == dw.DW_OK
+    del Ug, bg, xg
+    par = parity_of_sites(dims)
+    U16 = dw.gauge(dims, kappa, U, prec=dw.DW_F16, compress12=1)
+    full = np.where((par == 0)[:, None, None], b, 0)
+    x = dw.spinor(dims, b[par == 0], kind=dw.DW_SPINOR_EVEN, prec=dw.DW_F16)
+    out = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=dw.DW_F16)
+    for dag in (False, True):
+        n2 = dw.apply_norm(U16, x, out, dag=dag)
+        ref = O.schur(dims, kappa, U, full, parity=0, dag=dag)[par == 0]
+        assert site_err(out.download(), ref) <= 4e-3
+        ref2 = float(np.vdot(ref.reshape(-1), ref.reshape(-1)).real)
+        assert abs(n2[0] - ref2) <= 8e-3 * ref2
+        dw.apply(U16, x, out, dag=dag)
+        assert site_err(out.download(), ref) <= 4e-3
+
+
 def test_medium_workload(dw):
     dims, kappa, U, b = I.make_workload("wilson_16x16x16x32_exp0.4")
     Ug = dw.gauge(dims, kappa, U)

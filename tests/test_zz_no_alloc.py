@@ -13,7 +13,9 @@ from paper_2001_05218_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-13, "f32": 1e-6, "df64": 1e-13, "f16": 1e-6, "i16": 1e-6}  # same kernels: equal up to rounding order
+TOL = {"f64": 1e-13, "f32": 1e-6, "df64": 1e-13, "f16": 1e-6, "bf16": 1e-6, "i16": 1e-6}  # same kernels as dw_apply
+# against the FP64 oracle: the per-site bounds of the operator parity tests
+TOL_ORACLE = {"f64": 1e-13, "df64": 1e-13, "f32": 1e-6, "f16": 4e-3, "bf16": 3e-2, "i16": 2e-4}
 
 
 @pytest.fixture(scope="module")
@@ -24,17 +26,20 @@ def dw():
     return m
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32", "df64", "f16", "i16"])
+@pytest.mark.parametrize("prec,c12", [("f64", 0), ("f32", 0), ("df64", 0), ("f16", 0), ("i16", 0),
+                                      ("bf16", 0), ("f16", 1), ("bf16", 1), ("f32", 1)])
 @pytest.mark.parametrize("dagger", [0, 1])
-def test_noalloc_matches_dw_apply_on_two_calls(dw, prec, dagger):
+def test_noalloc_matches_dw_apply_on_two_calls(dw, prec, c12, dagger):
+    from oracle import oracle as O
     dims, kappa = (8, 6, 4, 10), 0.1234
     P = dw.PREC[prec]
     U = I.gauge_field(dims, "exp", 71, 1, 0.5)
     par = parity_of_sites(dims)
-    Ug = dw.gauge(dims, kappa, U, prec=P)
+    Ug = dw.gauge(dims, kappa, U, prec=P, compress12=c12)
     outs = []
     for call in range(2):  # two different sources in a row through the same scratch
-        psi = I.gaussian_spinor(dims, 71, 10 + call)[par == 0]
+        psi_full = I.gaussian_spinor(dims, 71, 10 + call)
+        psi = psi_full[par == 0]
         x = dw.spinor(dims, psi, kind=dw.DW_SPINOR_EVEN, prec=P)
         ref = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=P)
         got = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=P)
@@ -42,8 +47,27 @@ def test_noalloc_matches_dw_apply_on_two_calls(dw, prec, dagger):
         dw.check(dw.dw_apply_noalloc(Ug.handle, x.handle, got.handle, dagger, dw.current_stream()))
         g, r = got.download(), ref.download()
         assert site_err(g, r) <= TOL[prec]
+        full = np.where((par == 0)[:, None, None], psi_full, 0)
+        oref = O.schur(dims, kappa, U, full, parity=0, dag=bool(dagger))[par == 0]
+        assert site_err(g, oref) <= TOL_ORACLE[prec]
         outs.append(g)
     assert not np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("prec", ["f64", "f16"])
+def test_noalloc_full_lattice(dw, prec):
+    """Full-lattice fields take no scratch: D on all sites in one launch."""
+    from oracle import oracle as O
+    dims, kappa = (6, 10, 6, 6), 0.12
+    P = dw.PREC[prec]
+    U = I.gauge_field(dims, "haar", 73, 1)
+    psi = I.gaussian_spinor(dims, 73, 2)
+    Ug = dw.gauge(dims, kappa, U, prec=P, compress12=1 if prec == "f16" else 0)
+    x = dw.spinor(dims, psi, prec=P)
+    got = dw.spinor(dims, prec=P)
+    for dagger in (0, 1):
+        dw.check(dw.dw_apply_noalloc(Ug.handle, x.handle, got.handle, dagger, dw.current_stream()))
+        assert site_err(got.download(), O.dirac(dims, kappa, U, psi, dag=bool(dagger))) <= TOL_ORACLE[prec]
 
 
 def test_noalloc_multi_rhs_odd_parity(dw):
