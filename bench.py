@@ -187,16 +187,27 @@ def oracle_iteration_seconds(dims, kappa, U, b, reps):
 
 
 def cpu_baseline(workload, dims, kappa, U, b, iters_needed, budget_s=20.0):
+    """The oracle timed on all host cores (the reported value) and on one
+    core, per CGNR iteration, scaled by the iterations its CGNR needs."""
     from oracle import oracle as O
     O.build()
+    cores = O.num_threads()
     t1 = oracle_iteration_seconds(dims, kappa, U, b, 1)
     reps = max(1, min(20, int(budget_s / max(t1, 1e-3))))
     t = oracle_iteration_seconds(dims, kappa, U, b, reps)
     solve_s = t * iters_needed
-    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": O.num_threads(), "kind": "oracle",
+    O.set_num_threads(1)
+    try:
+        t_one = oracle_iteration_seconds(dims, kappa, U, b, 1)
+    finally:
+        O.set_num_threads(cores)
+    return {"value": 1.0 / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": "%d+1 CGNR iterations (D then D^dag, FP64, full lattice %s) of the oracle, %.3f s each, "
                       "scaled by the %d iterations plain FP64 CGNR needs on this system" %
-                      (reps, "x".join(map(str, dims)), t, iters_needed)}
+                      (reps, "x".join(map(str, dims)), t, iters_needed),
+            "single_core": {"value": 1.0 / (t_one * iters_needed), "unit": "solves/s", "cores": 1,
+                            "s_per_iteration": t_one,
+                            "sample": "1 CGNR iteration on one host core, scaled the same way"}}
 
 
 def run_reference(args):
@@ -255,7 +266,10 @@ def run_dslash(args):
     y = dw.spinor(dims, kind=dw.DW_SPINOR_EVEN, prec=prec, nrhs=args.nrhs)
     l2 = torch.cuda.get_device_properties(0).L2_cache_size
     scratch = torch.empty(2 * l2, dtype=torch.uint8, device="cuda")
-    op = dw.laplace_apply if args.op == "laplace" else dw.apply
+    if args.norm:  # the reducing epilogue: out and |out|^2 (FP64 grid reduction) in the second launch
+        op = lambda U_, x_, y_: dw.apply_norm(U_, x_, y_)  # noqa: E731
+    else:
+        op = dw.laplace_apply if args.op == "laplace" else dw.apply
     for _ in range(max(1, args.warmup)):
         op(Ug, x, y)
     torch.cuda.synchronize()
@@ -265,7 +279,8 @@ def run_dslash(args):
         op(Ug, x, y)
     prof, launches = dw.profile_stop()
     peak, kind = peaks()
-    out = {"mode": "dslash", "op": args.op, "workload": args.workload, "prec": args.dslash, "compress12": c12,
+    out = {"mode": "dslash", "op": args.op + ("+norm" if args.norm else ""), "workload": args.workload,
+           "prec": args.dslash, "compress12": c12,
            "nrhs": args.nrhs,
            "kernels": {}}
     for k, e in prof.items():
@@ -276,6 +291,65 @@ def run_dslash(args):
                              "gflops": e["flops"] / e["launches"] / pl / 1e6}
     out["peak_gbs"] = peak
     print(json.dumps(out))
+
+
+# ---------------------------------------------------------------------- host transfer mode
+def run_copies(args):
+    """Host<->device copy times of the end-to-end step's buffers (U and b up,
+    x down) with plain PyTorch copies between page-locked host memory and
+    device memory, each synchronised and timed on the host; no library call.
+    Shows the platform's copy rate per step, including its occasional slow
+    steps.  Not the benchmark line."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2001_05218_gb300 import inputs as I
+    dims = I.WORKLOADS[args.workload]["dims"]
+    V = int(np.prod(dims))
+    nU, nb = V * 4 * 9 * 2, V * 12 * 2  # float64 counts of complex128 U and one spinor
+    Uh = torch.empty(nU, dtype=torch.float64).pin_memory()
+    bh = torch.empty(nb, dtype=torch.float64).pin_memory()
+    xh = torch.empty(nb, dtype=torch.float64).pin_memory()
+    Ud = torch.empty(nU, dtype=torch.float64, device="cuda")
+    bd = torch.empty(nb, dtype=torch.float64, device="cuda")
+
+    def t(fn):
+        a = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - a) * 1e3
+
+    rows = []
+    for _ in range(args.warmup + args.steps):
+        rows.append([t(lambda: Ud.copy_(Uh, non_blocking=True)), t(lambda: bd.copy_(bh, non_blocking=True)),
+                     t(lambda: xh.copy_(bd, non_blocking=True))])
+    rows = np.array(rows[args.warmup:])
+    med = np.median(rows, axis=0)
+    gb = np.array([nU * 8, nb * 8, nb * 8]) / 1e9
+    out = {"mode": "copies", "workload": args.workload, "bytes": [int(v * 1e9) for v in gb],
+           "median_ms": med.round(3).tolist(), "median_gbs": (gb / (med / 1e3)).round(1).tolist(),
+           "max_ms": rows.max(axis=0).round(3).tolist(),
+           "slow_steps": [i for i, r in enumerate(rows) if np.any(r > 2 * med)],
+           "step_ms": rows.round(2).tolist()}
+    print(json.dumps(out))
+
+
+def measured_fp64_gflops(n=4096, reps=3):
+    """FP64 rate measured here: cuBLAS DGEMM (2 n^3 flops) through torch."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b_ = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b_)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(reps):
+        e0.record()
+        torch.matmul(a, b_)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return 2.0 * n ** 3 / (best / 1e3) / 1e9
 
 
 # ---------------------------------------------------------------------- all workloads
@@ -424,9 +498,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--dslash", default=None, help="stencil-only mode: f64|f32|f16|bf16|i16|df64 (Schur operator applies)")
     ap.add_argument("--nrhs", type=int, default=1, help="stencil-only mode: right-hand sides per field")
+    ap.add_argument("--norm", action="store_true",
+                    help="stencil-only mode: second launch with the reducing epilogue (dw_apply_norm)")
     ap.add_argument("--op", default="wilson", choices=["wilson", "laplace"],
                     help="stencil-only mode: the Wilson operator or the covariant Laplacian")
     ap.add_argument("--suite", action="store_true", help="time every workload configuration (not the benchmark line)")
+    ap.add_argument("--copies", action="store_true", help="host<->device copy times of the e2e buffers (not the benchmark line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -434,6 +511,8 @@ def main():
         return run_dslash(args)
     if args.suite:
         return run_suite(args)
+    if args.copies:
+        return run_copies(args)
 
     import torch
     rank, world, local = rank_info()
@@ -511,6 +590,25 @@ def main():
     solve_ms = float(np.mean(step_ms))
     st0 = stats[-1]
 
+    # the configuration as written for this workload: the same mixed solve with
+    # IEEE-FP64 (not double-float) reliable updates, median of three solves
+    outer64 = None
+    if args.outer != "f64" and not args.no_fp64:
+        p_m64 = dw.params(tol=1e-10, inner=inner, compress12=c12, maxiter=40000, outer="f64")
+        solve(p_m64)
+        ts, st64m = [], None
+        for _ in range(3):
+            reset_x()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st64m = dw.cg_solve(Ug, bg, xg, p_m64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        outer64 = {"ms": float(np.median(ts)), "iters": st64m[0]["iters"],
+                   "reliable_updates": st64m[0]["reliable_updates"], "true_rel_resid": st64m[0]["true_rel_resid"],
+                   "outer": "f64 (IEEE accumulator and reliable-update residual)", "statistic": "median of 3"}
+
     # per-launch stencil times: one more solve of the same system, stepped from
     # the host with CUDA events around every stencil launch on its stream
     reset_x()
@@ -520,7 +618,7 @@ def main():
     dw.cg_solve(Ug, bg, xg, p_mix)
     prof, _ = dw.profile_stop()
     peak_hbm, peak_kind = peaks()
-    peak_fp64 = 1250.0  # GFLOP/s, nominal GB300 FP64 (FMA = 2 flops)
+    peak_fp64 = measured_fp64_gflops()  # GFLOP/s, cuBLAS DGEMM measured on this GPU
 
     def roof(name, e):
         pl_ms = e["total_ms"] / e["launches"]
@@ -529,7 +627,7 @@ def main():
         gfl = e["flops"] / e["launches"] / (pl_ms / 1e3) / 1e9
         if name.startswith("hop f64"):
             return {"bound": "alu", "kernel": name, "achieved": gfl, "peak": peak_fp64, "unit": "GFLOP/s",
-                    "frac": gfl / peak_fp64, "peak_kind": "nominal FP64 (DFMA) rate", "traffic": None,
+                    "frac": gfl / peak_fp64, "peak_kind": "measured FP64 rate (cuBLAS DGEMM)", "traffic": None,
                     "bytes_per_launch": bpl, "ms_per_launch": pl_ms, "launches": e["launches"], "achieved_gbs": gbs,
                     "frac_hbm": gbs / peak_hbm}
         return {"bound": "hbm", "kernel": name, "achieved": gbs, "peak": peak_hbm, "unit": "GB/s",
@@ -648,10 +746,13 @@ def main():
                    "l2": "flushed between steps" if flush else "inputs larger than L2 (%d MB working set)" %
                          (working_set >> 20)},
         "mixed_cg": {"ms": solve_ms, "iters": st0["iters"], "reliable_updates": st0["reliable_updates"],
-                     "true_rel_resid": st0["true_rel_resid"]},
+                     "true_rel_resid": st0["true_rel_resid"], "ms_median": float(np.median(step_ms)),
+                     "ms_max": float(np.max(step_ms)), "step_ms": [round(v, 3) for v in step_ms]},
+        "mixed_cg_outer_f64": outer64,
         "fp64_cg": fp64,
         "speedup_vs_fp64": (fp64["ms"] / solve_ms) if fp64 else None,
         "roofline": roof(dom_name, dom),
+        "fp64_peak_gflops": peak_fp64,
         "roofline_inner": roof(inner_name[0], prof[inner_name[0]]) if inner_name else None,
         "stencil_profile": {"note": "one host-stepped solve with CUDA events around every stencil launch",
                             "kernels": {k: {"launches": v["launches"], "ms": v["total_ms"]} for k, v in prof.items()},

@@ -539,3 +539,14 @@ int or_num_threads(void) {
   return 1;
 #endif
 }
+
+/* Thread count of the oracle's OpenMP loops (n >= 1); used to time the
+ * oracle on one host core as well as on all of them. */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+  extern void omp_set_num_threads(int);
+  omp_set_num_threads(n < 1 ? 1 : n);
+#else
+  (void)n;
+#endif
+}

@@ -57,6 +57,7 @@ def lib():
             ("or_force", [P, I, D, P, P, P], None),
             ("or_su3_project", [ctypes.c_long, P, P, P], None),
             ("or_num_threads", [], I),
+            ("or_set_num_threads", [I], None),
         ]:
             f = getattr(L, name)
             f.argtypes = args
@@ -190,3 +191,8 @@ def su3_project(G, U):
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Thread count of the oracle's OpenMP loops."""
+    lib().or_set_num_threads(int(n))

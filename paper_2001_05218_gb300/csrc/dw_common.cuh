@@ -397,10 +397,23 @@ struct Spin<P64> {
       v[k] = cx(t.x, t.y);
     }
   }
-  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<double> (&v)[12]) {
+  // a site's stored words, formed in registers before they are written
+  struct Packed {
+    double2 w[12];
+  };
+  __device__ static __forceinline__ Packed pack(const Cx<double> (&v)[12]) {
+    Packed o;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o.w[k] = make_double2(v[k].re, v[k].im);
+    return o;
+  }
+  __device__ static __forceinline__ void store_packed(char* base, int vh, int s, const Packed& o) {
     double2* b = reinterpret_cast<double2*>(base);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) b[(size_t)k * vh + s] = make_double2(v[k].re, v[k].im);
+    for (int k = 0; k < 12; ++k) b[(size_t)k * vh + s] = o.w[k];
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<double> (&v)[12]) {
+    store_packed(base, vh, s, pack(v));
   }
   // v <- the value a store followed by a load would give
   __device__ static __forceinline__ void roundtrip(Cx<double> (&)[12]) {}
@@ -420,11 +433,22 @@ struct Spin<P32> {
       v[2 * k + 1] = cx(t.z, t.w);
     }
   }
-  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&v)[12]) {
+  struct Packed {
+    float4 w[6];
+  };
+  __device__ static __forceinline__ Packed pack(const Cx<float> (&v)[12]) {
+    Packed o;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) o.w[k] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+    return o;
+  }
+  __device__ static __forceinline__ void store_packed(char* base, int vh, int s, const Packed& o) {
     float4* b = reinterpret_cast<float4*>(base);
 #pragma unroll
-    for (int k = 0; k < 6; ++k)
-      b[(size_t)k * vh + s] = make_float4(v[2 * k].re, v[2 * k].im, v[2 * k + 1].re, v[2 * k + 1].im);
+    for (int k = 0; k < 6; ++k) b[(size_t)k * vh + s] = o.w[k];
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&v)[12]) {
+    store_packed(base, vh, s, pack(v));
   }
   __device__ static __forceinline__ void roundtrip(Cx<float> (&)[12]) {}
 };
@@ -487,20 +511,31 @@ struct Spin16 {
       v[4 * k + 3] = cx(e.x * sc, e.y * sc);
     }
   }
-  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&v)[12]) {
-    float m = site_max(v);
-    const float inv = m > 0.f ? 1.0f / m : 0.f;
-    uint4* b = reinterpret_cast<uint4*>(base);
+  struct Packed {
+    uint4 w[3];
+    float m;
+  };
+  __device__ static __forceinline__ Packed pack(const Cx<float> (&v)[12]) {
+    Packed o;
+    o.m = site_max(v);
+    const float inv = o.m > 0.f ? 1.0f / o.m : 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      uint4 t;
-      t.x = H16<P>::from2(v[4 * k + 0].re * inv, v[4 * k + 0].im * inv);
-      t.y = H16<P>::from2(v[4 * k + 1].re * inv, v[4 * k + 1].im * inv);
-      t.z = H16<P>::from2(v[4 * k + 2].re * inv, v[4 * k + 2].im * inv);
-      t.w = H16<P>::from2(v[4 * k + 3].re * inv, v[4 * k + 3].im * inv);
-      b[(size_t)k * vh + s] = t;
+      o.w[k].x = H16<P>::from2(v[4 * k + 0].re * inv, v[4 * k + 0].im * inv);
+      o.w[k].y = H16<P>::from2(v[4 * k + 1].re * inv, v[4 * k + 1].im * inv);
+      o.w[k].z = H16<P>::from2(v[4 * k + 2].re * inv, v[4 * k + 2].im * inv);
+      o.w[k].w = H16<P>::from2(v[4 * k + 3].re * inv, v[4 * k + 3].im * inv);
     }
-    reinterpret_cast<float*>(base + (size_t)48 * vh)[s] = m;
+    return o;
+  }
+  __device__ static __forceinline__ void store_packed(char* base, int vh, int s, const Packed& o) {
+    uint4* b = reinterpret_cast<uint4*>(base);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) b[(size_t)k * vh + s] = o.w[k];
+    reinterpret_cast<float*>(base + (size_t)48 * vh)[s] = o.m;
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<float> (&v)[12]) {
+    store_packed(base, vh, s, pack(v));
   }
   __device__ static __forceinline__ void roundtrip(Cx<float> (&v)[12]) {
     const float m = site_max(v);
@@ -535,10 +570,22 @@ struct Spin<PDF> {
       v[k].im = df_make(t.z, t.w);
     }
   }
-  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<DF> (&v)[12]) {
+  struct Packed {
+    float4 w[12];
+  };
+  __device__ static __forceinline__ Packed pack(const Cx<DF> (&v)[12]) {
+    Packed o;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) o.w[k] = make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
+    return o;
+  }
+  __device__ static __forceinline__ void store_packed(char* base, int vh, int s, const Packed& o) {
     float4* b = reinterpret_cast<float4*>(base);
 #pragma unroll
-    for (int k = 0; k < 12; ++k) b[(size_t)k * vh + s] = make_float4(v[k].re.hi, v[k].re.lo, v[k].im.hi, v[k].im.lo);
+    for (int k = 0; k < 12; ++k) b[(size_t)k * vh + s] = o.w[k];
+  }
+  __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<DF> (&v)[12]) {
+    store_packed(base, vh, s, pack(v));
   }
   __device__ static __forceinline__ void roundtrip(Cx<DF> (&)[12]) {}
 };
@@ -776,6 +823,11 @@ __device__ __forceinline__ int fdiv(int n, FastDiv f) {
 
 struct SysDesc {
   int lxh, ly, lz, lt;  // Lx/2, Ly, Lz, Lt
+  // kappa and kappa^2 as FP32 (kappa_f = fl(kappa), kappa2_f = fl(kappa^2)) and
+  // the low parts of their double-float forms, formed once on the host: GB300's
+  // FP64 pipe (about two operations per clock per SM) makes a per-thread
+  // double-to-float conversion cost microseconds per launch
+  float kappa_f, kappa2_f, kappa_lo, kappa2_lo;
   FastDiv div_lxh, div_ly, div_lz;
   int vh;               // sites per parity
   int nrhs;
@@ -784,8 +836,6 @@ struct SysDesc {
   int tile0;            // first block (within one parity) of this system
   int col0;             // first column (system, rhs) index
   int part0;            // first partial-sum slot (one per block and column)
-  int part2_0;          // first group-sum slot (one per group of kRedGroup blocks and column)
-  int cnt0;             // first arrival counter: [cnt0] groups done, [cnt0 + 1 + g] blocks of group g
   int sys;              // system index
   double kappa;
   Slot f[kNumSlots];
@@ -814,6 +864,7 @@ __device__ __forceinline__ int block_system(const Batch& B, int b) {
 struct ColState {
   double gamma;    // |z|^2, z = A-side residual
   double alpha, beta;
+  float alpha_f, beta_f;  // alpha and beta rounded to FP32 by the finalizer
   double rr;       // iterated |r|^2
   double rr_ref;   // |r|^2 at the last reliable update
   double bnorm2;   // |b|^2 (full lattice)
@@ -859,7 +910,6 @@ enum Fin {
 
 struct RedArgs {
   double* partial;
-  int* counter;
   ColState* cols;
   Flags* flags;
   int fin;
@@ -902,6 +952,7 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
         deactivate(C, ra.flags, 7 /* DW_ERR_BREAKDOWN */);
       } else {
         C.alpha = C.gamma / v;
+        C.alpha_f = (float)C.alpha;
       }
       break;
     case FIN_UPDATE: {
@@ -951,21 +1002,18 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
       if (!C.active) break;
       C.gamma = v;
       C.beta = 0.0;
+      C.beta_f = 0.f;
       break;
     case FIN_BETA:
       if (!C.active) break;
       C.beta = C.restart ? 0.0 : v / C.gamma;
+      C.beta_f = (float)C.beta;
       C.restart = 0;
       C.gamma = v;
       break;
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 // Warp total in lane 0 only (other lanes hold partial sums), fixed order.  Only
 // the lanes whose partial is still needed add, 31 FP64 additions per warp
 // instead of the butterfly's 160: GB300 executes two FP64 thread operations per
@@ -980,102 +1028,110 @@ __device__ __forceinline__ double warp_sum_lane0(double v) {
   return v;
 }
 
-// Two-level deterministic grid reduction.  A block holds RB groups of T
+// Value reduced inside a block: double-float for FP32 and double-float
+// arithmetic (added on the FP32 pipes, about 48 significant bits), IEEE FP64
+// for FP64 arithmetic.  Block partials and both grid levels are IEEE FP64.
+template <typename R>
+struct RedT {
+  using type = DF;
+};
+template <>
+struct RedT<double> {
+  using type = double;
+};
+__device__ __forceinline__ DF to_red(float v) { return df_make(v, 0.f); }
+__device__ __forceinline__ DF to_red(DF v) { return v; }
+__device__ __forceinline__ double to_red(double v) { return v; }
+__device__ __forceinline__ double red_double(DF v) { return (double)v; }
+__device__ __forceinline__ double red_double(double v) { return v; }
+__device__ __forceinline__ DF red_zero(DF) { return df_make(0.f, 0.f); }
+__device__ __forceinline__ double red_zero(double) { return 0.0; }
+// warp total in lane 0, fixed order, double-float on the FP32 pipes
+__device__ __forceinline__ DF warp_sum_lane0(DF v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float th = __shfl_down_sync(0xffffffffu, v.hi, o);
+    const float tl = __shfl_down_sync(0xffffffffu, v.lo, o);
+    if (lane < o) v = v + df_make(th, tl);
+  }
+  return v;
+}
+
+// Deterministic grid reduction in two kernels.  A block holds RB groups of T
 // threads (T a multiple of 32); group g works on right-hand side
-// r = blockIdx.y*RB + g.  Each group's values are summed in a fixed order and
-// written as the block's partial.  Blocks are grouped by tile, kRedGroup tiles
-// per group: the last block of a group to arrive (per-group arrival counter)
-// sums the group's partials of every column in a fixed order, and the last
-// group to finish sums the group sums and runs the finalizer.  Each level
-// reads at most kRedGroup values per column, so the serial tail stays short,
-// and every sum has a fixed order, so results are bitwise reproducible.
-// Every thread of the block must call this.
-constexpr int kRedGroup = 128;
-
-// Sum of n values (n <= kRedGroup * 2) of one column in a fixed order by the
-// threads of one warp (lane-strided, then a fixed butterfly).
-__device__ __forceinline__ double warp_sum_column(const double* p, int n, int lane) {
-  double s = 0.0;
-  for (int i = lane; i < n; i += 32) s += __ldcg(p + i);
-  return warp_sum(s);
-}
-
-// Sum over columns of the values p[r * stride + i], i < n, r < ncol; result
-// per column goes to fn(r, sum), called by one thread.  Fixed order.
-template <class Fn>
-__device__ __forceinline__ void sum_columns(const double* p, int stride, int n, int ncol, Fn fn, double* wsum) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nw = (int)(blockDim.x >> 5);
-  if (ncol >= nw) {
-    for (int r = warp; r < ncol; r += nw) {
-      const double s = warp_sum_column(p + r * stride, n, lane);
-      if (lane == 0) fn(r, s);
-    }
-    __syncthreads();
-    return;
-  }
-  for (int r = 0; r < ncol; ++r) {
-    double s = 0.0;
-    for (int i = tid; i < n; i += blockDim.x) s += __ldcg(p + r * stride + i);
-    s = warp_sum(s);
-    __syncthreads();
-    if (lane == 0) wsum[warp] = s;
-    __syncthreads();
-    if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < nw; ++w) t += wsum[w];
-      fn(r, t);
-    }
-  }
-  __syncthreads();
-}
-
-__device__ __forceinline__ void reduce_finalize(const SysDesc& S, int T, int RB, int tile, int ntiles, double v,
-                                                const RedArgs& ra) {
-  __shared__ double wsum[32];
-  __shared__ int am_last;
+// r = blockIdx.y*RB + g.  The producing kernel sums each group's values in a
+// fixed order (double-float on the FP32 pipes, or IEEE FP64 for FP64
+// arithmetic) and writes one IEEE-FP64 partial per block and right-hand side;
+// nothing in it waits.  k_finish, launched next on the same stream (which
+// orders the partial writes before it), sums each column's partials in a
+// fixed order and runs the finalizer.  Results are bitwise reproducible.
+// (A last-block-finishes scheme needs a fence and an arrival atomic in every
+// block, whose round trips hold the block's SM slot: measured on GB300, that
+// tail cost a 1M-site FP16 stencil about 25 us per launch.)
+//
+// `store` runs in every thread after the partials are written: a kernel
+// writes its outputs there.  Every thread of the block must call this.
+struct NoStore {
+  __device__ void operator()() const {}
+};
+template <class V, class Store = NoStore>
+__device__ __forceinline__ void reduce_block(const SysDesc& S, int T, int RB, int tile, int ntiles, V v,
+                                             const RedArgs& ra, int by, Store store = Store()) {
+  __shared__ V wpart[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   v = warp_sum_lane0(v);
-  if (lane == 0) wsum[warp] = v;
+  if (lane == 0) wpart[warp] = v;
   __syncthreads();
-  const int wpr = T >> 5;
   if (tid < RB) {
-    const int r = blockIdx.y * RB + tid;
+    const int r = by * RB + tid;
+    const int wpr = T >> 5;
     if (r < S.nrhs) {
-      double s = 0.0;
-      for (int w = 0; w < wpr; ++w) s += wsum[tid * wpr + w];
-      ra.partial[S.part0 + r * ntiles + tile] = s;
+      V s = wpart[tid * wpr];
+      for (int w = 1; w < wpr; ++w) s = s + wpart[tid * wpr + w];
+      ra.partial[S.part0 + r * ntiles + tile] = red_double(s);
     }
-    // only the writers of partials fence (before thread 0's arrival below):
-    // a fence in every thread would hold each thread until its own output
-    // stores were acknowledged
-    __threadfence();
   }
-  __syncthreads();
-  const int g = tile / kRedGroup;
-  const int ngroups = (ntiles + kRedGroup - 1) / kRedGroup;
-  const int g0 = g * kRedGroup;
-  const int gsize = ntiles - g0 < kRedGroup ? ntiles - g0 : kRedGroup;
-  if (tid == 0) am_last = (atomicAdd(&ra.counter[S.cnt0 + 1 + g], 1) == gsize * (int)gridDim.y - 1);
-  __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  // level 1: this group's partials -> one group sum per column
-  double* part2 = ra.partial + S.part2_0;
-  sum_columns(ra.partial + S.part0 + g0, ntiles, gsize, S.nrhs,
-              [&](int r, double sum) { part2[r * ngroups + g] = sum; }, wsum);
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    ra.counter[S.cnt0 + 1 + g] = 0;
-    am_last = (atomicAdd(&ra.counter[S.cnt0], 1) == ngroups - 1);
+  store();
+}
+
+// Finishing kernel: one block (kFinishThreads threads) per column (system,
+// right-hand side).  Thread t sums partials t, t + kFinishThreads, ... in
+// order (double-float), loading eight at a time so that their L2 round trips
+// overlap, then a fixed warp tree and a fixed sum over warps; thread 0 runs
+// the finalizer in IEEE FP64.  Columns whose kernel was gated off hold stale
+// partials; the finalizer ignores them by the same state the gate tested
+// (active, do_rel, xzero).
+constexpr int kFinishThreads = 1024;
+static __global__ void __launch_bounds__(kFinishThreads) k_finish(const __grid_constant__ Batch B, int par_mode,
+                                                           RedArgs ra) {
+  __shared__ DF wpart[kFinishThreads / 32];
+  const int col = blockIdx.x;
+  const int nrhs = B.sd[0].nrhs;
+  const int si = col / nrhs, r = col - si * nrhs;
+  const SysDesc& S = B.sd[si];
+  const int ntiles = par_mode == 2 ? 2 * S.tpp : S.tpp;
+  const double* p = ra.partial + S.part0 + (size_t)r * ntiles;
+  DF v = df_make(0.f, 0.f);
+  for (int i0 = threadIdx.x; i0 < ntiles; i0 += 8 * kFinishThreads) {
+    double t[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j * kFinishThreads;
+      t[j] = i < ntiles ? __ldcg(p + i) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v = v + DF(t[j]);
   }
+  v = warp_sum_lane0(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wpart[warp] = v;
   __syncthreads();
-  if (!am_last) return;
-  __threadfence();
-  // level 2: group sums -> column totals -> finalizer
-  sum_columns(part2, ngroups, ngroups, S.nrhs, [&](int r, double sum) { finalize(ra, S.col0 + r, sum); }, wsum);
-  if (tid == 0) ra.counter[S.cnt0] = 0;
+  if (threadIdx.x == 0) {
+    DF t = wpart[0];
+    for (int w = 1; w < kFinishThreads / 32; ++w) t = t + wpart[w];
+    finalize(ra, S.col0 + r, (double)t);
+  }
 }
 
 // Cooperative copy of this block's system descriptor into shared memory.

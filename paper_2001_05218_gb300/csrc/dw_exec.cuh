@@ -56,7 +56,6 @@ struct Exec {
   RedArgs ra(int fin) const {
     RedArgs a;
     a.partial = rb.partial;
-    a.counter = rb.counter;
     a.cols = rb.cols;
     a.flags = rb.flags;
     a.fin = fin;
@@ -80,6 +79,30 @@ SolveCacheEntry* solve_cache_find(const std::vector<unsigned long long>& key);
 // Inserts; evicts the least recently used entries beyond a small limit (after
 // synchronising the device).  The returned pointer stays valid until the next insert.
 SolveCacheEntry* solve_cache_insert(SolveCacheEntry&& e);
+
+// The second kernel of a grid reduction: sums the partials of the kernel just
+// launched (par_mode as that kernel's) per column and runs finalizer fin.
+inline void finish(const Exec& E, int par_mode, int fin) {
+  Profiler& pr = profiler();
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  if (pr.on) pr.launches += 1;
+  if (pr.timing) {
+    ea = pr.event();
+    eb = pr.event();
+    cudaEventRecord(ea, E.st);
+  }
+  k_finish<<<E.P.ncols, kFinishThreads, 0, E.st>>>(E.P.B, par_mode, E.ra(fin));
+  if (pr.timing) {
+    cudaEventRecord(eb, E.st);
+    Profiler::Rec r;
+    r.cat = pr.category("reduction finish");
+    r.a = ea;
+    r.b = eb;
+    r.bytes = (double)E.P.partials * 8.0;
+    r.flops = 0.0;
+    pr.recs.push_back(r);
+  }
+}
 
 template <int SPA, int LP, bool C12, bool DAG, int OP = OP_WILSON, class In, class Epi>
 inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int fin = FIN_STORE0) {
@@ -114,12 +137,14 @@ inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int 
     r.flops = (OP == OP_LAPLACE ? 2280.0 : 1320.0) * sites;
     pr.recs.push_back(r);
   }
+  if (Epi::kReduce) finish(E, par_mode, fin);
 }
 
 template <int SP>
 inline void norm(const Exec& E, int par_mode, int slot, int fin) {
   count_launch();
   k_norm<SP><<<E.grid(par_mode), E.P.block, 0, E.st>>>(E.P.B, par_mode, slot, E.ra(fin));
+  finish(E, par_mode, fin);
 }
 
 }  // namespace dw

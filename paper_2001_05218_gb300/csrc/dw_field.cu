@@ -113,6 +113,11 @@ void geometry(SysDesc& S, const dw_lattice& l, int nrhs) {
   S.nrhs = nrhs;
   S.anti_t = l.t_antiperiodic ? 1 : 0;
   S.kappa = l.kappa;
+  const double k2 = l.kappa * l.kappa;
+  S.kappa_f = (float)l.kappa;
+  S.kappa_lo = (float)(l.kappa - (double)S.kappa_f);
+  S.kappa2_f = (float)k2;
+  S.kappa2_lo = (float)(k2 - (double)S.kappa2_f);
 }
 
 void default_block_shape(int nrhs, int* T, int* RB) {
@@ -137,7 +142,7 @@ void make_plan(Plan& P, const dw_lattice* lats, int n, int nrhs, int T, int RB) 
   P.B.nsys = P.nsys;
   P.B.T = T;
   P.B.RB = RB;
-  int tile = 0, part = 0, cnt = 0;
+  int tile = 0, part = 0;
   for (int i = 0; i < P.nsys; ++i) {
     SysDesc& S = P.B.sd[i];
     geometry(S, lats[i], nrhs);
@@ -148,16 +153,10 @@ void make_plan(Plan& P, const dw_lattice* lats, int n, int nrhs, int T, int RB) 
     S.sys = i;
     tile += S.tpp;
     part += nrhs * 2 * S.tpp;  // block partials (both-parity launches hold 2*tpp tiles)
-    const int ngroups = (2 * S.tpp + kRedGroup - 1) / kRedGroup;
-    S.part2_0 = part;
-    part += nrhs * ngroups;    // group sums
-    S.cnt0 = cnt;
-    cnt += 1 + ngroups;        // arrival counters
   }
   P.B.ntot = tile;
   P.ncols = P.nsys * nrhs;
   P.partials = part;
-  P.counters = cnt;
   const int gy = (nrhs + RB - 1) / RB;
   P.block = dim3(T * RB);
   P.grid1 = dim3(tile, gy);
@@ -423,10 +422,12 @@ static void tune_load_once() {
   loaded = true;
   FILE* f = fopen(tune_path().c_str(), "r");
   if (!f) return;
-  char key[512];
+  char line[640], key[512];
   int T, RB;
-  while (fscanf(f, "%511s %d %d", key, &T, &RB) == 3)
+  while (fgets(line, sizeof line, f)) {
+    if (sscanf(line, "%511s %d %d", key, &T, &RB) != 3) continue;
     if (T >= 32 && T <= 256 && T % 32 == 0 && RB >= 1 && T * RB <= 256) tune_table()[key] = BlockShape{T, RB};
+  }
   fclose(f);
 }
 std::string tune_key(const dw_lattice* lats, int n, int nrhs, int prec, int c12) {
@@ -437,7 +438,7 @@ std::string tune_key(const dw_lattice* lats, int n, int nrhs, int prec, int c12)
     snprintf(dev_name, sizeof dev_name, "%s", prop.name);
   for (char* c = dev_name; *c; ++c)
     if (*c == ' ') *c = '_';
-  std::string key = std::string(dev_name) + "/v3/" + prec_name(prec) + (c12 ? "c12" : "c18") + "/r" +
+  std::string key = std::string(dev_name) + "/v4/" + prec_name(prec) + (c12 ? "c12" : "c18") + "/r" +
                     std::to_string(nrhs);
   for (int i = 0; i < n; ++i)
     key += "/" + std::to_string(lats[i].dims[0]) + "x" + std::to_string(lats[i].dims[1]) + "x" +

@@ -76,8 +76,7 @@ void geometry(SysDesc& S, const dw_lattice& l, int nrhs);
 struct Plan {
   Batch B;
   int nsys = 0, nrhs = 1, ncols = 0;
-  int partials = 0;  // doubles in the partial-sum buffer (block partials and group sums)
-  int counters = 0;  // ints of arrival counters
+  int partials = 0;  // doubles in the partial-sum buffer (one per block and column)
   dim3 block, grid1, grid2;  // one parity / both parities
 };
 // T sites per block and RB right-hand sides per block (T*RB <= 256, T a
@@ -103,7 +102,6 @@ std::string tune_key(const dw_lattice* lats, int n, int nrhs, int prec, int c12)
 // Device scratch for reductions of one plan.
 struct RedBuf {
   double* partial = nullptr;
-  int* counter = nullptr;
   ColState* cols = nullptr;
   Flags* flags = nullptr;
 };

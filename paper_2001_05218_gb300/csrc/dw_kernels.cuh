@@ -18,6 +18,8 @@
 //   (1 + s gamma_mu) psi = [ h ; s B^dag h ],  h = psi_up + s B psi_down.
 #pragma once
 
+#include <type_traits>
+
 #include "dw_common.cuh"
 
 namespace dw {
@@ -32,6 +34,27 @@ enum Gate { G_ACTIVE = 0, G_REL, G_ALL, G_XZERO, G_ZSRC };
 template <int C>
 __device__ __forceinline__ double coef_of(double kappa) {
   return C == C_ONE ? 1.0 : C == C_MK ? -kappa : C == C_PK ? kappa : C == C_MK2 ? -kappa * kappa : kappa * kappa;
+}
+// The coefficient in the arithmetic type R, from the system's pre-rounded
+// kappa (FP32 and double-float) so that no thread converts from FP64.
+template <int C, typename R>
+__device__ __forceinline__ R coef(const SysDesc& S) {
+  if constexpr (std::is_same<R, double>::value) {
+    return coef_of<C>(S.kappa);
+  } else if constexpr (std::is_same<R, float>::value) {
+    return C == C_ONE ? 1.f : C == C_MK ? -S.kappa_f : C == C_PK ? S.kappa_f : C == C_MK2 ? -S.kappa2_f : S.kappa2_f;
+  } else {
+    const DF k = df_make(S.kappa_f, S.kappa_lo), k2 = df_make(S.kappa2_f, S.kappa2_lo);
+    return C == C_ONE ? DF(1) : C == C_MK ? -k : C == C_PK ? k : C == C_MK2 ? -k2 : k2;
+  }
+}
+// A CG scalar (alpha, beta) in the arithmetic type R: the finalizer's FP32
+// rounding for FP32, the FP64 value split exactly for double-float.
+template <typename R>
+__device__ __forceinline__ R scalar_as(double v, float vf) {
+  if constexpr (std::is_same<R, double>::value) return v;
+  else if constexpr (std::is_same<R, float>::value) return vf;
+  else return DF(v);
 }
 
 __device__ __forceinline__ int gate_of(int g, const ColState* cols, int col) {
@@ -446,17 +469,23 @@ struct InSum {
 };
 
 // ------------------------------------------------------------------ epilogues
+// write(): forms and stores the output of one site.  Reducing epilogues with
+// kSplit also offer prepare() (forms the stored words and the reduced value)
+// and commit() (stores them), so that the kernel can publish its block's
+// partial sum before the output stores.
 // out = coef * H in
 template <int SPO, int COEF>
 struct EpiOut {
   static constexpr bool kReduce = false;
+  static constexpr bool kSplit = false;
+  using Packed = int;
   int slot_out;
   int gate;
   __host__ double io_bytes() const { return Spin<SPO>::kBytes; }
-  template <typename R>
-  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12], double&) const {
+  template <typename R, typename V>
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12], V&) const {
     using RO = typename Spin<SPO>::R;
-    const R c = (R)coef_of<COEF>(S.kappa);
+    const R c = coef<COEF, R>(S);
     Cx<RO> o[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) o[k] = cx((RO)(c * acc[k].re), (RO)(c * acc[k].im));
@@ -469,15 +498,18 @@ struct EpiOut {
 template <int SPO, int SPX, int COEF, bool RED>
 struct EpiXpay {
   static constexpr bool kReduce = RED;
+  static constexpr bool kSplit = RED;
+  using Packed = typename Spin<SPO>::Packed;
   int slot_out, slot_x;
   int gate;
   __host__ double io_bytes() const { return Spin<SPX>::kBytes + (slot_out >= 0 ? Spin<SPO>::kBytes : 0); }
   template <typename R>
-  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12], double& nrm) const {
+  __device__ __forceinline__ Packed prepare(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12],
+                                            typename RedT<R>::type& nrm) const {
     using RO = typename Spin<SPO>::R;
     Cx<typename Spin<SPX>::R> xv[12];
     Spin<SPX>::load(slot_ptr(S, slot_x, r, par), S.vh, s, xv);
-    const R c = (R)coef_of<COEF>(S.kappa);
+    const R c = coef<COEF, R>(S);
     Cx<RO> o[12];
     R n = (R)0;
 #pragma unroll
@@ -486,8 +518,17 @@ struct EpiXpay {
       o[k] = cx((RO)re, (RO)im);
       n = fma(re, re, fma(im, im, n));
     }
-    nrm = (double)n;
-    if (slot_out >= 0) Spin<SPO>::store(slot_wptr(S, slot_out, r, par), S.vh, s, o);
+    nrm = to_red(n);
+    return Spin<SPO>::pack(o);
+  }
+  __device__ __forceinline__ void commit(const SysDesc& S, int par, int r, int s, const Packed& o) const {
+    if (slot_out >= 0) Spin<SPO>::store_packed(slot_wptr(S, slot_out, r, par), S.vh, s, o);
+  }
+  template <typename R>
+  __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12],
+                                        typename RedT<R>::type& nrm) const {
+    const Packed o = prepare(S, par, r, s, acc, nrm);
+    commit(S, par, r, s, o);
   }
 };
 
@@ -496,15 +537,25 @@ struct EpiXpay {
 template <int SPO, int SPX, int COEF>
 struct EpiXpayDot {
   static constexpr bool kReduce = true;
+  static constexpr bool kSplit = true;
+  using Packed = typename Spin<SPO>::Packed;
   int slot_out, slot_x;
   int gate;
   __host__ double io_bytes() const { return Spin<SPX>::kBytes + Spin<SPO>::kBytes; }
+  __device__ __forceinline__ void commit(const SysDesc& S, int par, int r, int s, const Packed& o) const {
+    Spin<SPO>::store_packed(slot_wptr(S, slot_out, r, par), S.vh, s, o);
+  }
   template <typename R>
   __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12], double& nrm) const {
+    commit(S, par, r, s, prepare(S, par, r, s, acc, nrm));
+  }
+  template <typename R>
+  __device__ __forceinline__ Packed prepare(const SysDesc& S, int par, int r, int s, Cx<R> (&acc)[12],
+                                            typename RedT<R>::type& nrm) const {
     using RO = typename Spin<SPO>::R;
     Cx<typename Spin<SPX>::R> xv[12];
     Spin<SPX>::load(slot_ptr(S, slot_x, r, par), S.vh, s, xv);
-    const R c = (R)coef_of<COEF>(S.kappa);
+    const R c = coef<COEF, R>(S);
     Cx<RO> o[12];
     R n = (R)0;
 #pragma unroll
@@ -514,8 +565,8 @@ struct EpiXpayDot {
       o[k] = cx((RO)re, (RO)im);
       n = fma(xr, re, fma(xi, im, n));
     }
-    nrm = (double)n;
-    Spin<SPO>::store(slot_wptr(S, slot_out, r, par), S.vh, s, o);
+    nrm = to_red(n);
+    return Spin<SPO>::pack(o);
   }
 };
 
@@ -526,20 +577,22 @@ struct EpiXpayDot {
 template <int SPL, int SPA, int SPH>
 struct EpiReliableEO {
   static constexpr bool kReduce = true;
+  static constexpr bool kSplit = false;
+  using Packed = int;
   int gate;
   __host__ double io_bytes() const {
     return 3.0 * Spin<SPH>::kBytes + 2.0 * Spin<SPA>::kBytes + Spin<SPL>::kBytes;
   }
   template <typename RH>
   __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<RH> (&acc)[12],
-                                        double& nrm) const {
+                                        typename RedT<RH>::type& nrm) const {
     using RA = typename Spin<SPA>::R;
     Cx<RH> x[12], bh[12], rv[12];
     Cx<RA> xl[12];
     Spin<SPH>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
     Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
     Spin<SPH>::load(slot_ptr(S, S_BH, r, par), S.vh, s, bh);
-    const RH k2 = (RH)(S.kappa * S.kappa);
+    const RH k2 = coef<C_PK2, RH>(S);
     RH n = (RH)0;
     Cx<RA> zero[12];
 #pragma unroll
@@ -549,7 +602,7 @@ struct EpiReliableEO {
       n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
       zero[k] = cx((RA)0, (RA)0);
     }
-    nrm = (double)n;
+    nrm = to_red(n);
     Spin<SPH>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
     Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, zero);
     Cx<typename Spin<SPL>::R> lo[12];
@@ -564,6 +617,8 @@ struct EpiReliableEO {
 template <int SPL, bool STORE_LOW, int SPH>
 struct EpiResidFull {
   static constexpr bool kReduce = true;
+  static constexpr bool kSplit = false;
+  using Packed = int;
   int gate;
   int slot_rt;  // < 0: norm only
   int slot_x;
@@ -573,18 +628,18 @@ struct EpiResidFull {
   }
   template <typename RH>
   __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<RH> (&acc)[12],
-                                        double& nrm) const {
+                                        typename RedT<RH>::type& nrm) const {
     Cx<RH> x[12], b[12], rv[12];
     Spin<SPH>::load(slot_ptr(S, slot_x, r, par), S.vh, s, x);
     Spin<SPH>::load(slot_ptr(S, slot_b, r, par), S.vh, s, b);
-    const RH kap = (RH)S.kappa;
+    const RH kap = coef<C_PK, RH>(S);
     RH n = (RH)0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       rv[k] = cx(fma(kap, acc[k].re, b[k].re - x[k].re), fma(kap, acc[k].im, b[k].im - x[k].im));
       n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
     }
-    nrm = (double)n;
+    nrm = to_red(n);
     if (slot_rt >= 0) Spin<SPH>::store(slot_wptr(S, slot_rt, r, par), S.vh, s, rv);
     if (STORE_LOW) {
       Cx<typename Spin<SPL>::R> lo[12];
@@ -630,7 +685,15 @@ struct EpiResidFull {
   {                                                                        \
     const int ntiles = par_mode == 2 ? 2 * S.tpp : S.tpp;                  \
     const int tt = par_mode == 2 ? par * S.tpp + tile : tile;              \
-    reduce_finalize(S, T, RB, tt, ntiles, val, ra);                        \
+    reduce_block(S, T, RB, tt, ntiles, val, ra, blockIdx.y);               \
+  }
+// As DW_BLOCK_REDUCE, with the output stores STORE (a lambda) run after the
+// block's partial sums are written.
+#define DW_BLOCK_REDUCE_STORE(val, STORE)                                  \
+  {                                                                        \
+    const int ntiles = par_mode == 2 ? 2 * S.tpp : S.tpp;                  \
+    const int tt = par_mode == 2 ? par * S.tpp + tile : tile;              \
+    reduce_block(S, T, RB, tt, ntiles, val, ra, blockIdx.y, STORE);        \
   }
 
 // ------------------------------------------------------------------ the Laplacian's directions
@@ -722,18 +785,20 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
     k_hop(const __grid_constant__ Batch B, int par_mode, int link_slot, In in, Epi epi, RedArgs ra) {
   using R = typename Spin<SPA>::R;
   DW_BLOCK_PROLOGUE(epi.gate)
-  double nrm = 0.0;
-  if (valid) {
-    const Coord c = coord_of(S, s, par);
-    const int pin = par ^ 1;
-    const char* ulink_own = slot_ptr(S, link_slot, 0, par);  // links based at this site
-    const char* ulink_nb = slot_ptr(S, link_slot, 0, pin);   // links based at the neighbour
-    const long long mu_stride = (long long)Link<LP, C12>::kBytes * S.vh;
-    constexpr int SF = DAG ? +1 : -1;  // forward projector sign
-    constexpr int SB = -SF;            // backward projector sign
-    Cx<R> acc[12];
+  {
+    typename RedT<R>::type nrm = red_zero(typename RedT<R>::type());
+    typename Epi::Packed po;
+    if (valid) {
+      const Coord c = coord_of(S, s, par);
+      const int pin = par ^ 1;
+      const char* ulink_own = slot_ptr(S, link_slot, 0, par);  // links based at this site
+      const char* ulink_nb = slot_ptr(S, link_slot, 0, pin);   // links based at the neighbour
+      const long long mu_stride = (long long)Link<LP, C12>::kBytes * S.vh;
+      constexpr int SF = DAG ? +1 : -1;  // forward projector sign
+      constexpr int SB = -SF;            // backward projector sign
+      Cx<R> acc[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) acc[k] = cx((R)0, (R)0);
+      for (int k = 0; k < 12; ++k) acc[k] = cx((R)0, (R)0);
 
 #define DW_HOP_DIR(MU)                                                          \
   {                                                                             \
@@ -771,62 +836,66 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
     su3_mul_w<true, SPA>(u, h, g);                                              \
     accumulate_w<MU, SB>(acc, g, eta < 0.f ? -sc : sc);                         \
   }
-    if constexpr (OP == OP_LAPLACE) {
-      laplace_dirs<SPA, LP, C12>(S, in, c, s, r, pin, ulink_own, ulink_nb, mu_stride, acc);
-      if constexpr (SPA == PDF) {
+      if constexpr (OP == OP_LAPLACE) {
+        laplace_dirs<SPA, LP, C12>(S, in, c, s, r, pin, ulink_own, ulink_nb, mu_stride, acc);
+        if constexpr (SPA == PDF) {
+#pragma unroll
+          for (int k = 0; k < 12; ++k) acc[k] = cx(renorm(acc[k].re), renorm(acc[k].im));
+        }
+      } else if constexpr (SPA == P16 || SPA == PB16) {
+        DW_HOP_DIR_W(0)
+        DW_HOP_DIR_W(1)
+        DW_HOP_DIR_W(2)
+        DW_HOP_DIR_W(3)
+      } else if constexpr (SPA == PDF) {
+        // compact loop: one copy of the double-float mat-vec per (U, U^dag)
+#pragma unroll 1
+        for (int mu = 0; mu < 4; ++mu) {
+          float eta;
+          Cx<R> p[12], h[6], g[6], u[9];
+          const DirSpin df = dir_spin(mu, SF), db = dir_spin(mu, SB);
+          const int nf = neighbour_rt(S, c, s, mu, +1, &eta);
+          in.load(S, pin, r, nf, p);
+          project_rt(df, p, h);
+          Link<LP, C12>::load(ulink_own + mu * mu_stride, S.vh, s, u);
+          if (eta < 0.f) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im);
+          }
+          su3_mul<false>(u, h, g);
+          accumulate_rt(df, acc, g);
+          const int nb = neighbour_rt(S, c, s, mu, -1, &eta);
+          in.load(S, pin, r, nb, p);
+          project_rt(db, p, h);
+          Link<LP, C12>::load(ulink_nb + mu * mu_stride, S.vh, nb, u);
+          if (eta < 0.f) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im);
+          }
+          su3_mul<true>(u, h, g);
+          accumulate_rt(db, acc, g);
+        }
 #pragma unroll
         for (int k = 0; k < 12; ++k) acc[k] = cx(renorm(acc[k].re), renorm(acc[k].im));
+      } else {
+        DW_HOP_DIR(0)
+        DW_HOP_DIR(1)
+        DW_HOP_DIR(2)
+        DW_HOP_DIR(3)
       }
-    } else
-#ifndef DW_HOP16_CONVERT
-    if constexpr (SPA == P16 || SPA == PB16) {
-      DW_HOP_DIR_W(0)
-      DW_HOP_DIR_W(1)
-      DW_HOP_DIR_W(2)
-      DW_HOP_DIR_W(3)
-    } else
-#endif
-    if constexpr (SPA == PDF) {
-      // compact loop: one copy of the double-float mat-vec per (U, U^dag)
-#pragma unroll 1
-      for (int mu = 0; mu < 4; ++mu) {
-        float eta;
-        Cx<R> p[12], h[6], g[6], u[9];
-        const DirSpin df = dir_spin(mu, SF), db = dir_spin(mu, SB);
-        const int nf = neighbour_rt(S, c, s, mu, +1, &eta);
-        in.load(S, pin, r, nf, p);
-        project_rt(df, p, h);
-        Link<LP, C12>::load(ulink_own + mu * mu_stride, S.vh, s, u);
-        if (eta < 0.f) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im);
-        }
-        su3_mul<false>(u, h, g);
-        accumulate_rt(df, acc, g);
-        const int nb = neighbour_rt(S, c, s, mu, -1, &eta);
-        in.load(S, pin, r, nb, p);
-        project_rt(db, p, h);
-        Link<LP, C12>::load(ulink_nb + mu * mu_stride, S.vh, nb, u);
-        if (eta < 0.f) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) h[k] = cx(-h[k].re, -h[k].im);
-        }
-        su3_mul<true>(u, h, g);
-        accumulate_rt(db, acc, g);
-      }
-#pragma unroll
-      for (int k = 0; k < 12; ++k) acc[k] = cx(renorm(acc[k].re), renorm(acc[k].im));
-    } else {
-      DW_HOP_DIR(0)
-      DW_HOP_DIR(1)
-      DW_HOP_DIR(2)
-      DW_HOP_DIR(3)
-    }
 #undef DW_HOP_DIR
 #undef DW_HOP_DIR_W
-    epi.write(S, par, r, s, acc, nrm);
+      if constexpr (Epi::kSplit) po = epi.prepare(S, par, r, s, acc, nrm);
+      else epi.write(S, par, r, s, acc, nrm);
+    }
+    if constexpr (Epi::kSplit) {
+      DW_BLOCK_REDUCE_STORE(nrm, [&] {
+        if (valid) epi.commit(S, par, r, s, po);
+      })
+    } else if constexpr (Epi::kReduce) {
+      DW_BLOCK_REDUCE(nrm)
+    }
   }
-  if (Epi::kReduce) DW_BLOCK_REDUCE(nrm)
 }
 
 // ------------------------------------------------------------------ site-local kernels
@@ -834,36 +903,43 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
 template <int SPL, int SPA>
 __global__ void __launch_bounds__(256) k_update_xr(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_ACTIVE)
-  double nrm = 0.0;
+  using RL = typename Spin<SPL>::R;
+  using RA = typename Spin<SPA>::R;
+  typename RedT<RL>::type nrm = red_zero(typename RedT<RL>::type());
+  typename Spin<SPA>::Packed xlp;
+  typename Spin<SPL>::Packed rp;
   if (valid) {
-    using RL = typename Spin<SPL>::R;
-    using RA = typename Spin<SPA>::R;
-    const double alpha = ra.cols[S.col0 + r].alpha;
+    const ColState& C = ra.cols[S.col0 + r];
     Cx<RL> p[12], w[12], rv[12];
     Cx<RA> xl[12];
     Spin<SPL>::load(slot_ptr(S, S_P, r, par), S.vh, s, p);
     Spin<SPL>::load(slot_ptr(S, S_W, r, par), S.vh, s, w);
     Spin<SPL>::load(slot_ptr(S, S_R, r, par), S.vh, s, rv);
     Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
-    const RL a = (RL)alpha;
-    const RA aa = (RA)alpha;
+    const RL a = scalar_as<RL>(C.alpha, C.alpha_f);
+    const RA aa = scalar_as<RA>(C.alpha, C.alpha_f);
     RL n = (RL)0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       xl[k] = cx(fma(aa, (RA)p[k].re, xl[k].re), fma(aa, (RA)p[k].im, xl[k].im));
       rv[k] = cx(fma(-a, w[k].re, rv[k].re), fma(-a, w[k].im, rv[k].im));
     }
-    Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, xl);
+    xlp = Spin<SPA>::pack(xl);
     // the norm is taken of the value as stored, so the recursion sees what
     // the next kernels will read
     Spin<SPL>::roundtrip(rv);
-    Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, rv);
+    rp = Spin<SPL>::pack(rv);
 #pragma unroll
     for (int k = 0; k < 12; ++k) n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
-    nrm = (double)n;
+    nrm = to_red(n);
   }
   ra.fin = FIN_UPDATE;
-  DW_BLOCK_REDUCE(nrm)
+  DW_BLOCK_REDUCE_STORE(nrm, [&] {
+    if (valid) {
+      Spin<SPA>::store_packed(slot_wptr(S, S_XL, r, par), S.vh, s, xlp);
+      Spin<SPL>::store_packed(slot_wptr(S, S_R, r, par), S.vh, s, rp);
+    }
+  })
 }
 
 // p = z + beta p
@@ -872,7 +948,7 @@ __global__ void __launch_bounds__(256) k_update_p(const __grid_constant__ Batch 
   DW_BLOCK_PROLOGUE(G_ACTIVE)
   if (valid) {
     using RL = typename Spin<SPL>::R;
-    const RL beta = (RL)ra.cols[S.col0 + r].beta;
+    const RL beta = scalar_as<RL>(ra.cols[S.col0 + r].beta, ra.cols[S.col0 + r].beta_f);
     Cx<RL> p[12], z[12];
     Spin<SPL>::load(slot_ptr(S, S_P, r, par), S.vh, s, p);
     Spin<SPL>::load(slot_ptr(S, S_Z, r, par), S.vh, s, z);
@@ -886,15 +962,16 @@ __global__ void __launch_bounds__(256) k_update_p(const __grid_constant__ Batch 
 template <int SPL, int SPH>
 __global__ void __launch_bounds__(256) k_init_r(const __grid_constant__ Batch B, int par_mode, int slot_src, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_XZERO)
-  double nrm = 0.0;
+  using RH = typename Spin<SPH>::R;
+  typename RedT<RH>::type nrm = red_zero(typename RedT<RH>::type());
   if (valid) {
-    using RH = typename Spin<SPH>::R;
     Cx<RH> v[12];
     Cx<typename Spin<SPL>::R> lo[12];
     Spin<SPH>::load(slot_ptr(S, slot_src, r, par), S.vh, s, v);
+    RH n = (RH)0;
 #pragma unroll
-    for (int k = 0; k < 12; ++k)
-      nrm = fma((double)v[k].re, (double)v[k].re, fma((double)v[k].im, (double)v[k].im, nrm));
+    for (int k = 0; k < 12; ++k) n = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, n));
+    nrm = to_red(n);
     convert12(v, lo);
     Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, lo);
   }
@@ -926,14 +1003,34 @@ __global__ void __launch_bounds__(256) k_fold_x(const __grid_constant__ Batch B,
 template <int SP>
 __global__ void __launch_bounds__(256) k_norm(const __grid_constant__ Batch B, int par_mode, int slot, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_ALL)
-  double nrm = 0.0;
+  using RS = typename Spin<SP>::R;
+  typename RedT<RS>::type nrm = red_zero(typename RedT<RS>::type());
   if (valid) {
-    Cx<typename Spin<SP>::R> v[12];
+    Cx<RS> v[12];
     Spin<SP>::load(slot_ptr(S, slot, r, par), S.vh, s, v);
+    RS n = (RS)0;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) nrm = fma((double)v[k].re, (double)v[k].re, fma((double)v[k].im, (double)v[k].im, nrm));
+    for (int k = 0; k < 12; ++k) n = fma(v[k].re, v[k].re, fma(v[k].im, v[k].im, n));
+    nrm = to_red(n);
   }
   DW_BLOCK_REDUCE(nrm)
+}
+
+// Odd-site reconstruction x_o = b_o + kappa t_o, t_o = H_oe x_e as left in the
+// odd half of S_RT by the last reliable update, in the high precision SPH.
+template <int SPH>
+__global__ void __launch_bounds__(256) k_recon_odd(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
+  DW_BLOCK_PROLOGUE(G_ALL)
+  if (valid) {
+    using RH = typename Spin<SPH>::R;
+    Cx<RH> bv[12], tv[12], xv[12];
+    Spin<SPH>::load(slot_ptr(S, S_B, r, par), S.vh, s, bv);
+    Spin<SPH>::load(slot_ptr(S, S_RT, r, par), S.vh, s, tv);
+    const RH k = coef<C_PK, RH>(S);
+#pragma unroll
+    for (int j = 0; j < 12; ++j) xv[j] = cx(fma(k, tv[j].re, bv[j].re), fma(k, tv[j].im, bv[j].im));
+    Spin<SPH>::store(slot_wptr(S, S_X, r, par), S.vh, s, xv);
+  }
 }
 
 // field <- 0 for the columns with a zero source (gate G_ZSRC)

@@ -19,27 +19,25 @@ extern "C" dw_status dw_apply_norm(const dw_field* U, const dw_field* in, dw_fie
   S.f[S_AUX0] = spinor_slot(in);
   S.f[S_AUX2] = spinor_slot(out);
   // one pool allocation: the Schur intermediate (parity fields) and the
-  // reduction buffers (partial sums, arrival counters, column states, flags)
+  // reduction buffers (partial sums, column states, flags)
   auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const size_t tmp_b =
       in->kind == DW_SPINOR_FULL ? 0 : al((size_t)in->nrhs * spin_bytes(in->prec) * vh_of(in->lat));
-  const size_t part_b = al(sizeof(double) * E.P.partials), cnt_b = al(sizeof(int) * E.P.counters);
+  const size_t part_b = al(sizeof(double) * E.P.partials);
   const size_t cols_b = al(sizeof(ColState) * E.P.ncols), flags_b = al(sizeof(Flags));
   char* buf = nullptr;
-  DW_CUDA(cudaMallocAsync((void**)&buf, tmp_b + part_b + cnt_b + cols_b + flags_b, st));
+  DW_CUDA(cudaMallocAsync((void**)&buf, tmp_b + part_b + cols_b + flags_b, st));
   char* p = buf;
   if (tmp_b) S.f[S_AUX1] = arena_slot(p, in->lat, in->prec, in->nrhs, 1);
   p += tmp_b;
   E.rb.partial = reinterpret_cast<double*>(p);
   p += part_b;
-  E.rb.counter = reinterpret_cast<int*>(p);
-  p += cnt_b;
   E.rb.cols = reinterpret_cast<ColState*>(p);
   p += cols_b;
   E.rb.flags = reinterpret_cast<Flags*>(p);
   std::vector<ColState> hc(E.P.ncols);
-  cudaError_t e = cudaMemsetAsync(E.rb.counter, 0, sizeof(int) * E.P.counters, st);
-  dw_status s = e == cudaSuccess ? apply_dispatch<true>(E, U, in, dagger) : cuda_error(e, "cudaMemsetAsync", __FILE__, __LINE__);
+  dw_status s = apply_dispatch<true>(E, U, in, dagger);
+  cudaError_t e;
   if (s == DW_OK) {
     e = cudaMemcpyAsync(hc.data(), E.rb.cols, sizeof(ColState) * hc.size(), cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) s = cuda_error(e, "cudaMemcpyAsync(norms)", __FILE__, __LINE__);

@@ -187,6 +187,7 @@ dw_status CG<L, A, C12, H, OP>::build_graph(const Exec& E0, int mode, cudaGraphE
   count_launch();
   count_launch();
   k_update_xr<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_UPDATE));
+  finish(E, pm, FIN_UPDATE);
   k_cond_rel<<<1, 1, 0, E.st>>>(E.rb.flags, hr);
   {
     cudaStreamCaptureStatus cst;
@@ -253,6 +254,7 @@ dw_status CG<L, A, C12, H, OP>::run_stepped(const Exec& E, int mode, int maxiter
     wstep(E, mode);
     count_launch();
     k_update_xr<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_UPDATE));
+    finish(E, pm, FIN_UPDATE);
     DW_CUDA(cudaMemcpyAsync(hf, E.rb.flags, sizeof(Flags), cudaMemcpyDeviceToHost, E.st));
     DW_CUDA(cudaStreamSynchronize(E.st));
     if (hf->rel_pending > 0) reliable(E, mode);
@@ -339,14 +341,11 @@ dw_status CG<L, A, C12, H, OP>::run(const SolveArgs& a) {
         total += al((size_t)nrhs * pc.npar * spin_bytes(pc.prec) * vh);
       }
     }
-    const size_t red_bytes = al(sizeof(double) * F.P.partials) + al(sizeof(int) * F.P.counters) +
-                             al(sizeof(ColState) * F.P.ncols) + al(sizeof(Flags));
+    const size_t red_bytes = al(sizeof(double) * F.P.partials) + al(sizeof(ColState) * F.P.ncols) + al(sizeof(Flags));
     DW_CUDA(cudaMalloc((void**)&fresh.arena, total + red_bytes));
     char* rp = fresh.arena + total;
     F.rb.partial = reinterpret_cast<double*>(rp);
     rp += al(sizeof(double) * F.P.partials);
-    F.rb.counter = reinterpret_cast<int*>(rp);
-    rp += al(sizeof(int) * F.P.counters);
     F.rb.cols = reinterpret_cast<ColState*>(rp);
     rp += al(sizeof(ColState) * F.P.ncols);
     F.rb.flags = reinterpret_cast<Flags*>(rp);
@@ -364,6 +363,13 @@ dw_status CG<L, A, C12, H, OP>::run(const SolveArgs& a) {
       if (mode == MODE_NORMAL || mode == MODE_HERM) S.f[S_Z] = S.f[S_R];
       for (auto pc : {S_XL, S_P})
         fresh.zero.push_back({S.f[pc].p, (size_t)nrhs * fpar * (pc == S_XL ? spin_bytes(A) : spin_bytes(L)) * S.vh});
+      // odd half of the high-precision temporary: holds H_oe x_e after every
+      // reliable update and feeds the odd-site reconstruction; zero for a
+      // column that converges before its first one (x_e = 0 there)
+      if (eo)
+        for (int r = 0; r < nrhs; ++r)
+          fresh.zero.push_back({S.f[S_RT].p + r * S.f[S_RT].rhs_stride + S.f[S_RT].par_stride,
+                                (size_t)spin_bytes(H) * S.vh});
     }
     F.st = st;
     dw_status gs = build_graph(F, mode, &fresh.exec, &fresh.body_k, &fresh.rel_k);
@@ -400,7 +406,6 @@ dw_status CG<L, A, C12, H, OP>::run(const SolveArgs& a) {
   DW_CUDA(cudaEventRecord(ev0, st));
   DW_CUDA(cudaMemcpyAsync(E.rb.cols, hc.data(), sizeof(ColState) * hc.size(), cudaMemcpyHostToDevice, st));
   DW_CUDA(cudaMemcpyAsync(E.rb.flags, &hf, sizeof hf, cudaMemcpyHostToDevice, st));
-  DW_CUDA(cudaMemsetAsync(E.rb.counter, 0, sizeof(int) * E.P.counters, st));
   if (a.p.timeout_s > 0) {
     count_launch();
     k_set_deadline<<<(E.P.ncols + 127) / 128, 128, 0, st>>>(E.rb.cols, E.P.ncols,
@@ -424,6 +429,7 @@ dw_status CG<L, A, C12, H, OP>::run(const SolveArgs& a) {
   // zero guess: r = source (bh or b); otherwise r = source - A x, recomputed
   count_launch();
   k_init_r<L, H><<<E.grid(eo ? 0 : 2), E.P.block, 0, st>>>(E.P.B, eo ? 0 : 2, eo ? S_BH : S_B, E.ra(FIN_RESID0));
+  finish(E, eo ? 0 : 2, FIN_RESID0);
   if (profiler().timing) {
     // host-stepped (profiled) run: launch the first FP64-class residual only
     // when the guess is non-zero, so every timed launch does its work
@@ -451,7 +457,10 @@ dw_status CG<L, A, C12, H, OP>::run(const SolveArgs& a) {
 
   // ---- finish: odd sites, then the IEEE FP64 residual from the caller's fields
   if (eo) {
-    hop<H, H, false, false, OP>(E, 1, kLinkHi, InOne<H>{S_X}, EpiXpay<H, H, C_PK, false>{S_X, S_B, G_ALL});
+    // x_o = b_o + kappa H_oe x_e, with H_oe x_e (the first hop of the column's
+    // last reliable update, taken of its final x_e) read from the odd half of S_RT
+    count_launch();
+    k_recon_odd<H><<<E.grid(1), E.P.block, 0, st>>>(E.P.B, 1, E.ra(FIN_STORE0));
   }
   if (H != P64) {
     count_launch();

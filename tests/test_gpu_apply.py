@@ -296,3 +296,4 @@ def test_double_float_conversion_accuracy(dw):
     assert np.all(back[0] == 0)
     rel = np.abs(back - psi) / np.maximum(np.abs(psi), 1e-300)
     assert rel[1:].max() <= 2.0 ** -47
+
