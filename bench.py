@@ -330,6 +330,32 @@ def run_copies(args):
            "max_ms": rows.max(axis=0).round(3).tolist(),
            "slow_steps": [i for i, r in enumerate(rows) if np.any(r > 2 * med)],
            "step_ms": rows.round(2).tolist()}
+    # the same copies split into k chunks on k streams (separate copy engines)
+    split = {}
+    for k in (2, 4, 8):
+        streams = [torch.cuda.Stream() for _ in range(k)]
+
+        def chunked(dst, src):
+            n = dst.numel()
+            step = (n + k - 1) // k
+            cur = torch.cuda.current_stream()
+            ev = torch.cuda.Event()
+            ev.record(cur)
+            for i, st_ in enumerate(streams):
+                st_.wait_event(ev)
+                with torch.cuda.stream(st_):
+                    dst[i * step:(i + 1) * step].copy_(src[i * step:(i + 1) * step], non_blocking=True)
+            for st_ in streams:
+                cur.wait_stream(st_)
+
+        ts = []
+        for _ in range(args.warmup + args.steps):
+            ts.append([t(lambda: chunked(Ud, Uh)), t(lambda: chunked(xh, bd))])
+        ts = np.array(ts[args.warmup:])
+        m = np.median(ts, axis=0)
+        split[str(k)] = {"median_ms": m.round(3).tolist(),
+                         "median_gbs": (gb[[0, 2]] / (m / 1e3)).round(1).tolist()}
+    out["split_streams"] = split
     print(json.dumps(out))
 
 

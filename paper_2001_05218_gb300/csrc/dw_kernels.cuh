@@ -444,30 +444,6 @@ struct InOne {
   }
 };
 
-// Neighbour spinor x + xl: the high-precision accumulator plus the
-// low-precision increment.
-template <int SPH, int SPL>
-struct InSum {
-  static constexpr bool kScaled = false;
-  int slot_x, slot_xl;
-  __host__ double io_bytes() const { return Spin<SPH>::kBytes + Spin<SPL>::kBytes; }
-  template <typename R>
-  __device__ __forceinline__ void load(const SysDesc& S, int par, int r, int s, Cx<R> (&v)[12]) const {
-    using RH = typename Spin<SPH>::R;
-    Cx<RH> a[12];
-    Cx<typename Spin<SPL>::R> b[12];
-    Spin<SPH>::load(slot_ptr(S, slot_x, r, par), S.vh, s, a);
-    Spin<SPL>::load(slot_ptr(S, slot_xl, r, par), S.vh, s, b);
-#pragma unroll
-    for (int k = 0; k < 12; ++k) v[k] = cx((R)(a[k].re + (RH)b[k].re), (R)(a[k].im + (RH)b[k].im));
-  }
-  template <typename R>
-  __device__ __forceinline__ void load_raw(const SysDesc& S, int par, int r, int s, Cx<R> (&v)[12], R& sc) const {
-    load(S, par, r, s, v);
-    sc = (R)1;
-  }
-};
-
 // ------------------------------------------------------------------ epilogues
 // write(): forms and stores the output of one site.  Reducing epilogues with
 // kSplit also offer prepare() (forms the stored words and the reduced value)
@@ -570,41 +546,32 @@ struct EpiXpayDot {
   }
 };
 
-// Reliable update on the even-odd system, in the high precision SPH, at even site s:
-//   x <- x + xl;  xl <- 0;  r_hi = bh - x + kappa^2 * acc  (acc = H_eo t_hi);
-//   r_low <- r_hi;  reduction |r_hi|^2.  r_hi itself is not stored: the
-//   iteration continues from r_low, and the next correction recomputes r_hi.
-template <int SPL, int SPA, int SPH>
-struct EpiReliableEO {
+// Residual of the even-odd system in the high precision SPH at even site s,
+// once the accumulator x has absorbed the low-precision increment:
+//   r_hi = bh - x + kappa^2 * acc  (acc = H_eo t, t = H_oe x);  r_low <- r_hi;
+//   reduction |r_hi|^2.  r_hi itself is not stored: the iteration continues
+//   from r_low, and the next correction recomputes r_hi.
+template <int SPL, int SPH>
+struct EpiResidEO {
   static constexpr bool kReduce = true;
   static constexpr bool kSplit = false;
   using Packed = int;
   int gate;
-  __host__ double io_bytes() const {
-    return 3.0 * Spin<SPH>::kBytes + 2.0 * Spin<SPA>::kBytes + Spin<SPL>::kBytes;
-  }
+  __host__ double io_bytes() const { return 2.0 * Spin<SPH>::kBytes + Spin<SPL>::kBytes; }
   template <typename RH>
   __device__ __forceinline__ void write(const SysDesc& S, int par, int r, int s, Cx<RH> (&acc)[12],
                                         typename RedT<RH>::type& nrm) const {
-    using RA = typename Spin<SPA>::R;
     Cx<RH> x[12], bh[12], rv[12];
-    Cx<RA> xl[12];
     Spin<SPH>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
-    Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
     Spin<SPH>::load(slot_ptr(S, S_BH, r, par), S.vh, s, bh);
     const RH k2 = coef<C_PK2, RH>(S);
     RH n = (RH)0;
-    Cx<RA> zero[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      x[k] = cx(x[k].re + (RH)xl[k].re, x[k].im + (RH)xl[k].im);
       rv[k] = cx(fma(k2, acc[k].re, bh[k].re - x[k].re), fma(k2, acc[k].im, bh[k].im - x[k].im));
       n = fma(rv[k].re, rv[k].re, fma(rv[k].im, rv[k].im, n));
-      zero[k] = cx((RA)0, (RA)0);
     }
     nrm = to_red(n);
-    Spin<SPH>::store(slot_wptr(S, S_X, r, par), S.vh, s, x);
-    Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, zero);
     Cx<typename Spin<SPL>::R> lo[12];
     convert12(rv, lo);
     Spin<SPL>::store(slot_wptr(S, S_R, r, par), S.vh, s, lo);
@@ -978,7 +945,7 @@ __global__ void __launch_bounds__(256) k_init_r(const __grid_constant__ Batch B,
   DW_BLOCK_REDUCE(nrm)
 }
 
-// x += xl; xl = 0   (full-lattice reliable update, both parities)
+// x += xl; xl = 0 on the launched parities (start of a reliable update)
 template <int SPA, int SPH>
 __global__ void __launch_bounds__(256) k_fold_x(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_REL)

@@ -70,12 +70,18 @@ struct CG {
 
   // reliable update (gated by do_rel) and its finalizer
   static void reliable(const Exec& E, int mode) {
-    if constexpr (OP == OP_LAPLACE) {  // MODE_HERM: r = bh - x + k^2 K_eo K_oe x, as MODE_EO
-      hop<H, H, false, false, OP>(E, 1, kLinkHi, InSum<H, A>{S_X, S_XL}, EpiOut<H, C_ONE>{S_RT, G_REL});
-      hop<H, H, false, false, OP>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiReliableEO<L, A, H>{G_REL}, FIN_RELIABLE);
+    // even-odd systems: x_e += xl_e (xl_e = 0); t_o = H_oe x_e; r_e = bh - x_e + k^2 H_eo t_o
+    // (MODE_HERM: the same with the Laplacian's K)
+    auto eo_reliable = [&] {
+      count_launch();
+      k_fold_x<A, H><<<E.grid(0), E.P.block, 0, E.st>>>(E.P.B, 0, E.ra(FIN_STORE0));
+      hop<H, H, false, false, OP>(E, 1, kLinkHi, InOne<H>{S_X}, EpiOut<H, C_ONE>{S_RT, G_REL});
+      hop<H, H, false, false, OP>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiResidEO<L, H>{G_REL}, FIN_RELIABLE);
+    };
+    if constexpr (OP == OP_LAPLACE) {
+      eo_reliable();
     } else if (mode == MODE_EO) {
-      hop<H, H, false, false, OP>(E, 1, kLinkHi, InSum<H, A>{S_X, S_XL}, EpiOut<H, C_ONE>{S_RT, G_REL});
-      hop<H, H, false, false, OP>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiReliableEO<L, A, H>{G_REL}, FIN_RELIABLE);
+      eo_reliable();
     } else if (mode == MODE_FULL) {
       count_launch();
       k_fold_x<A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
