@@ -1095,6 +1095,32 @@ __device__ __forceinline__ void reduce_block(const SysDesc& S, int T, int RB, in
   store();
 }
 
+// As reduce_block for a thread holding the values of NV consecutive right-hand
+// sides, (by*RB + g)*NV + j for its group g and j < NV.
+template <int NV, class V, class Store = NoStore>
+__device__ __forceinline__ void reduce_block_n(const SysDesc& S, int T, int RB, int tile, int ntiles,
+                                               const V (&v)[NV], const RedArgs& ra, int by, Store store = Store()) {
+  __shared__ V wpart[NV][32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const V w = warp_sum_lane0(v[j]);
+    if (lane == 0) wpart[j][warp] = w;
+  }
+  __syncthreads();
+  if (tid < RB * NV) {
+    const int g = tid / NV, j = tid - g * NV;
+    const int r = (by * RB + g) * NV + j;
+    const int wpr = T >> 5;
+    if (r < S.nrhs) {
+      V s = wpart[j][g * wpr];
+      for (int w = 1; w < wpr; ++w) s = s + wpart[j][g * wpr + w];
+      ra.partial[S.part0 + r * ntiles + tile] = red_double(s);
+    }
+  }
+  store();
+}
+
 // Finishing kernel: one block (kFinishThreads threads) per column (system,
 // right-hand side).  Thread t sums partials t, t + kFinishThreads, ... in
 // order (double-float), loading eight at a time so that their L2 round trips

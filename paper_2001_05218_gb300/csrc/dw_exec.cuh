@@ -3,6 +3,7 @@
 
 #include <cstdio>
 #include <string>
+#include <type_traits>
 #include <utility>
 
 #include "dw_internal.h"
@@ -114,8 +115,18 @@ inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int 
     eb = pr.event();
     cudaEventRecord(ea, E.st);
   }
-  k_hop<SPA, LP, C12, DAG, In, Epi, OP><<<E.grid(par_mode), E.P.block, 0, E.st>>>(E.P.B, par_mode, link_slot, in,
-                                                                                  epi, E.ra(fin));
+  bool launched = false;
+  if constexpr ((SPA == P16 || SPA == PB16) && LP == SPA && OP == OP_WILSON && std::is_same<In, InOne<SPA>>::value) {
+    if (E.P.pair && E.P.nrhs >= 2) {  // two right-hand sides per thread, each link loaded once for both
+      dim3 g = E.grid(par_mode);
+      g.y = (E.P.nrhs + 2 * E.P.B.RB - 1) / (2 * E.P.B.RB);
+      k_hop_pair<SPA, C12, DAG, Epi><<<g, E.P.block, 0, E.st>>>(E.P.B, par_mode, link_slot, in.slot, epi, E.ra(fin));
+      launched = true;
+    }
+  }
+  if (!launched)
+    k_hop<SPA, LP, C12, DAG, In, Epi, OP><<<E.grid(par_mode), E.P.block, 0, E.st>>>(E.P.B, par_mode, link_slot, in,
+                                                                                    epi, E.ra(fin));
   if (pr.timing) {
     cudaEventRecord(eb, E.st);
     const int npar = par_mode == 2 ? 2 : 1;

@@ -136,6 +136,7 @@ void default_block_shape(int nrhs, int* T, int* RB) {
 
 void make_plan(Plan& P, const dw_lattice* lats, int n, int nrhs, int T, int RB) {
   memset(&P.B, 0, sizeof P.B);
+  P.pair = 0;
   P.nsys = n;
   P.nrhs = nrhs;
   if (T <= 0 || RB <= 0) default_block_shape(nrhs, &T, &RB);
@@ -423,10 +424,14 @@ static void tune_load_once() {
   FILE* f = fopen(tune_path().c_str(), "r");
   if (!f) return;
   char line[640], key[512];
-  int T, RB;
+  int T, RB, pair;
   while (fgets(line, sizeof line, f)) {
-    if (sscanf(line, "%511s %d %d", key, &T, &RB) != 3) continue;
-    if (T >= 32 && T <= 256 && T % 32 == 0 && RB >= 1 && T * RB <= 256) tune_table()[key] = BlockShape{T, RB};
+    if (sscanf(line, "%511s %d %d %d", key, &T, &RB, &pair) != 4) continue;
+    if (T >= 32 && T <= 256 && T % 32 == 0 && RB >= 1 && T * RB <= 256 && (pair == 0 || pair == 1)) {
+      BlockShape b{T, RB};
+      b.pair = pair;
+      tune_table()[key] = b;
+    }
   }
   fclose(f);
 }
@@ -438,7 +443,7 @@ std::string tune_key(const dw_lattice* lats, int n, int nrhs, int prec, int c12)
     snprintf(dev_name, sizeof dev_name, "%s", prop.name);
   for (char* c = dev_name; *c; ++c)
     if (*c == ' ') *c = '_';
-  std::string key = std::string(dev_name) + "/v4/" + prec_name(prec) + (c12 ? "c12" : "c18") + "/r" +
+  std::string key = std::string(dev_name) + "/v5/" + prec_name(prec) + (c12 ? "c12" : "c18") + "/r" +
                     std::to_string(nrhs);
   for (int i = 0; i < n; ++i)
     key += "/" + std::to_string(lats[i].dims[0]) + "x" + std::to_string(lats[i].dims[1]) + "x" +
@@ -466,7 +471,7 @@ void tune_store(const std::string& key, BlockShape v) {
   mkdir(cmd_dir.c_str(), 0755);
   FILE* f = fopen(path.c_str(), "a");
   if (f) {
-    fprintf(f, "%s %d %d\n", key.c_str(), v.T, v.RB);
+    fprintf(f, "%s %d %d %d\n", key.c_str(), v.T, v.RB, v.pair);
     fclose(f);
   }
 }

@@ -75,6 +75,7 @@ void geometry(SysDesc& S, const dw_lattice& l, int nrhs);
 // Launch plan for a set of systems sharing nrhs.
 struct Plan {
   Batch B;
+  int pair = 0;      // 16-bit Wilson stencils: two right-hand sides per thread (k_hop_pair)
   int nsys = 0, nrhs = 1, ncols = 0;
   int partials = 0;  // doubles in the partial-sum buffer (one per block and column)
   dim3 block, grid1, grid2;  // one parity / both parities
@@ -93,6 +94,7 @@ void default_block_shape(int nrhs, int* T, int* RB);
 // file named by DW_TUNE_CACHE (default ~/.cache/dwsolve/tune.txt).
 struct BlockShape {
   int T, RB;
+  int pair = 0;  // 16-bit stencils: each thread group takes two right-hand sides (grid.y halves)
 };
 bool tune_lookup(const std::string& key, BlockShape* out);
 void tune_store(const std::string& key, BlockShape v);

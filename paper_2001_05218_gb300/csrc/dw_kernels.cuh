@@ -670,7 +670,11 @@ template <int SPA, int LP, bool C12, class In, typename R>
 __device__ __forceinline__ void laplace_dirs(const SysDesc& S, const In& in, const Coord& c, int s, int r, int pin,
                                              const char* ulink_own, const char* ulink_nb, long long mu_stride,
                                              Cx<R> (&acc)[12]) {
-#pragma unroll 1
+  // FP32 and 16-bit: all eight directions unrolled (compile-time neighbour
+  // arithmetic); double-float and FP64 keep one copy of the loop body, whose
+  // unrolled form would not fit the instruction cache
+  constexpr int kUnroll = (SPA == PDF || SPA == P64) ? 1 : 8;
+#pragma unroll kUnroll
   for (int d = 0; d < 8; ++d) {
     const int mu = d >> 1;
     const bool fwd = (d & 1) == 0;
@@ -862,6 +866,105 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
     } else if constexpr (Epi::kReduce) {
       DW_BLOCK_REDUCE(nrm)
     }
+  }
+}
+
+// 16-bit stencil with two right-hand sides per thread: each link is loaded,
+// and with 12-real compression its third row rebuilt, once and applied to
+// both; the two neighbour loads of a direction are in flight together.  Block:
+// T sites x RB thread groups, group g of grid row y taking right-hand sides
+// 2(y RB + g) and 2(y RB + g) + 1; grid.y = ceil(nrhs / (2 RB)).
+template <int SPA, bool C12, bool DAG, class Epi>
+__global__ void __launch_bounds__(256, 2)
+    k_hop_pair(const __grid_constant__ Batch B, int par_mode, int link_slot, int in_slot, Epi epi, RedArgs ra) {
+  static_assert(SPA == P16 || SPA == PB16, "two right-hand sides per thread: 16-bit storage");
+  __shared__ SysDesc S;
+  __shared__ int act[64];
+  const int T = B.T, RB = B.RB;
+  int b = blockIdx.x, par;
+  if (par_mode == 2) {
+    par = b >= B.ntot ? 1 : 0;
+    b -= par * B.ntot;
+  } else {
+    par = par_mode;
+  }
+  load_desc(S, B.sd, block_system(B, b));
+  __syncthreads();
+  for (int i_ = threadIdx.x; i_ < S.nrhs; i_ += blockDim.x) act[i_] = gate_of(epi.gate, ra.cols, S.col0 + i_);
+  __syncthreads();
+  int any = 0;
+  for (int i_ = 0; i_ < S.nrhs; ++i_) any |= act[i_];
+  if (!any) return;
+  const int rl = threadIdx.x / T;
+  const int r0 = (blockIdx.y * RB + rl) * 2, r1 = r0 + 1;
+  const int tile = b - S.tile0;
+  const int s = tile * T + (threadIdx.x - rl * T);
+  const bool site = s < S.vh;
+  const bool v0 = site && r0 < S.nrhs && act[r0 < S.nrhs ? r0 : 0];
+  const bool v1 = site && r1 < S.nrhs && act[r1 < S.nrhs ? r1 : 0];
+  const int r1l = r1 < S.nrhs ? r1 : r0;  // a missing second column reloads the first
+  typename RedT<float>::type nrm[2] = {red_zero(typename RedT<float>::type()), red_zero(typename RedT<float>::type())};
+  typename Epi::Packed po0, po1;
+  if (v0 || v1) {
+    const InOne<SPA> in{in_slot};
+    const Coord c = coord_of(S, s, par);
+    const int pin = par ^ 1;
+    const char* ulink_own = slot_ptr(S, link_slot, 0, par);
+    const char* ulink_nb = slot_ptr(S, link_slot, 0, pin);
+    const long long mu_stride = (long long)Link<SPA, C12>::kBytes * S.vh;
+    constexpr int SF = DAG ? +1 : -1;
+    constexpr int SB = -SF;
+    Cx<float> acc0[12], acc1[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) acc0[k] = acc1[k] = cx(0.f, 0.f);
+#define DW_HOP_PAIR_DIR(MU)                                                     \
+  {                                                                             \
+    float eta, sc0, sc1;                                                        \
+    uint32_t p0[12], p1[12], h0[6], h1[6], u[9];                                \
+    Cx<float> g[6];                                                             \
+    const int nf = neighbour<MU, +1>(S, c, s, &eta);                            \
+    in.load_words(S, pin, r0, nf, p0, sc0);                                     \
+    in.load_words(S, pin, r1l, nf, p1, sc1);                                    \
+    Link<SPA, C12>::load_words(ulink_own + MU * mu_stride, S.vh, s, u);         \
+    project_w<MU, SF, SPA>(p0, h0);                                             \
+    project_w<MU, SF, SPA>(p1, h1);                                             \
+    su3_mul_w<false, SPA>(u, h0, g);                                            \
+    accumulate_w<MU, SF>(acc0, g, eta < 0.f ? -sc0 : sc0);                      \
+    su3_mul_w<false, SPA>(u, h1, g);                                            \
+    accumulate_w<MU, SF>(acc1, g, eta < 0.f ? -sc1 : sc1);                      \
+    const int nb = neighbour<MU, -1>(S, c, s, &eta);                            \
+    in.load_words(S, pin, r0, nb, p0, sc0);                                     \
+    in.load_words(S, pin, r1l, nb, p1, sc1);                                    \
+    Link<SPA, C12>::load_words(ulink_nb + MU * mu_stride, S.vh, nb, u);         \
+    project_w<MU, SB, SPA>(p0, h0);                                             \
+    project_w<MU, SB, SPA>(p1, h1);                                             \
+    su3_mul_w<true, SPA>(u, h0, g);                                             \
+    accumulate_w<MU, SB>(acc0, g, eta < 0.f ? -sc0 : sc0);                      \
+    su3_mul_w<true, SPA>(u, h1, g);                                             \
+    accumulate_w<MU, SB>(acc1, g, eta < 0.f ? -sc1 : sc1);                      \
+  }
+    DW_HOP_PAIR_DIR(0)
+    DW_HOP_PAIR_DIR(1)
+    DW_HOP_PAIR_DIR(2)
+    DW_HOP_PAIR_DIR(3)
+#undef DW_HOP_PAIR_DIR
+    if constexpr (Epi::kSplit) {
+      if (v0) po0 = epi.prepare(S, par, r0, s, acc0, nrm[0]);
+      if (v1) po1 = epi.prepare(S, par, r1, s, acc1, nrm[1]);
+    } else {
+      if (v0) epi.write(S, par, r0, s, acc0, nrm[0]);
+      if (v1) epi.write(S, par, r1, s, acc1, nrm[1]);
+    }
+  }
+  if constexpr (Epi::kReduce) {
+    const int ntiles = par_mode == 2 ? 2 * S.tpp : S.tpp;
+    const int tt = par_mode == 2 ? par * S.tpp + tile : tile;
+    reduce_block_n<2>(S, T, RB, tt, ntiles, nrm, ra, blockIdx.y, [&] {
+      if constexpr (Epi::kSplit) {
+        if (v0) epi.commit(S, par, r0, s, po0);
+        if (v1) epi.commit(S, par, r1, s, po1);
+      }
+    });
   }
 }
 

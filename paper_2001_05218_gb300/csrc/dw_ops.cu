@@ -19,6 +19,7 @@ void apply_plan(Plan& P, const dw_field* U, const dw_field* in) {
   BlockShape shape{0, 0};
   tune_lookup(tune_key(&U->lat, 1, in->nrhs, U->prec, U->compress12), &shape);
   make_plan(P, &U->lat, 1, in->nrhs, shape.T, shape.RB);
+  P.pair = shape.pair;
 }
 
 // One application of D (or D^dag) with temporaries from the stream-ordered pool.

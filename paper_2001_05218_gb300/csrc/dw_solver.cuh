@@ -320,6 +320,7 @@ dw_status CG<L, A, C12, H, OP>::run(const SolveArgs& a) {
     BlockShape shape{a.p.tile, a.p.tile > 0 ? 1 : 0};
     if (a.p.tile <= 0) shape = tune_inner_shape<L, C12>(lats, nrhs, lo_links, st);
     make_plan(F.P, lats, nrhs, shape.T, shape.RB);
+    F.P.pair = shape.pair;
     auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
     struct Piece { int slot, prec, npar; };
     std::vector<Piece> pieces;

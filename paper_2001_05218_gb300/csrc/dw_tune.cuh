@@ -31,6 +31,16 @@ BlockShape tune_inner_shape(const std::vector<dw_lattice>& lats, int nrhs, const
   for (int T : {32, 64, 128, 256})
     for (int RB = 1; RB <= nrhs && RB <= 12; ++RB)
       if (nrhs % RB == 0 && T * RB <= 256) cand.push_back(BlockShape{T, RB});
+  // 16-bit storage, several right-hand sides: also two per thread (each link
+  // loaded once for both), RB thread groups per block
+  if ((L == P16 || L == PB16) && nrhs >= 2 && nrhs % 2 == 0)
+    for (int T : {32, 64, 128, 256})
+      for (int RB = 1; 2 * RB <= nrhs && RB <= 6; ++RB)
+        if (nrhs % (2 * RB) == 0 && T * RB <= 256) {
+          BlockShape b{T, RB};
+          b.pair = 1;
+          cand.push_back(b);
+        }
 
   // temporary fields: three parity spinors per system (input, intermediate,
   // output) and the reduction buffers of the largest candidate plan
@@ -69,6 +79,7 @@ BlockShape tune_inner_shape(const std::vector<dw_lattice>& lats, int nrhs, const
     Exec E;
     E.st = st;
     E.P = plans[ci];
+    E.P.pair = c.pair;
     E.rb = rb;
     for (size_t i = 0; i < lats.size(); ++i) {
       SysDesc& S = E.P.B.sd[i];

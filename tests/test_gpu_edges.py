@@ -147,7 +147,7 @@ def test_bf16_multi_rhs_solve(dw):
 
 def test_tuning_cache_file_round_trip(dw, tmp_path, monkeypatch):
     """The autotuner's choices are appended to the tuning file as
-    'key T RB' lines with block shapes inside the launch limits."""
+    'key T RB pair' lines with block shapes inside the launch limits."""
     import os
     path = os.environ.get("DW_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "dwsolve", "tune.txt")
     dims, kappa = (4, 6, 4, 6), 0.12  # a shape no other test uses
@@ -157,9 +157,9 @@ def test_tuning_cache_file_round_trip(dw, tmp_path, monkeypatch):
     dw.cg_solve(Ug, bg, x, dw.params(tol=1e-10, inner="f32"))
     lines = [l.split() for l in open(path).read().splitlines() if "4x6x4x6" in l]
     assert lines
-    for key, T, RB in lines:
+    for key, T, RB, pair in lines:
         T, RB = int(T), int(RB)
-        assert T % 32 == 0 and 32 <= T <= 256 and RB >= 1 and T * RB <= 256
+        assert T % 32 == 0 and 32 <= T <= 256 and RB >= 1 and T * RB <= 256 and pair in ("0", "1")
 
 
 def test_solves_from_two_host_threads(dw):
