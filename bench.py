@@ -378,6 +378,34 @@ def measured_fp64_gflops(n=4096, reps=3):
     return 2.0 * n ** 3 / (best / 1e3) / 1e9
 
 
+def run_rates(args):
+    """FP64 and FP32 arithmetic rates of this GPU (cuBLAS DGEMM and SGEMM with
+    TF32 off, 2 n^3 flops, best of a few) beside the FP64 stencil's own rate:
+    the ALU rooflines of the IEEE-FP64 and FP32 stencils.  Not the benchmark
+    line."""
+    import torch
+    torch.cuda.set_device(0)
+    torch.backends.cuda.matmul.allow_tf32 = False
+    out = {"mode": "rates"}
+    for name, dt, n in (("dgemm_gflops", torch.float64, 4096), ("sgemm_gflops", torch.float32, 8192)):
+        a = torch.randn(n, n, dtype=dt, device="cuda")
+        b_ = torch.randn(n, n, dtype=dt, device="cuda")
+        torch.matmul(a, b_)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = None
+        for _ in range(3):
+            e0.record()
+            torch.matmul(a, b_)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        out[name] = 2.0 * n ** 3 / (best / 1e3) / 1e9
+    out["sm_count"] = torch.cuda.get_device_properties(0).multi_processor_count
+    print(json.dumps(out))
+
+
 # ---------------------------------------------------------------------- all workloads
 def run_suite(args):
     """Time-to-solution of every workload configuration, mixed precision
@@ -530,6 +558,7 @@ def main():
                     help="stencil-only mode: the Wilson operator or the covariant Laplacian")
     ap.add_argument("--suite", action="store_true", help="time every workload configuration (not the benchmark line)")
     ap.add_argument("--copies", action="store_true", help="host<->device copy times of the e2e buffers (not the benchmark line)")
+    ap.add_argument("--rates", action="store_true", help="FP64 and FP32 GEMM rates of this GPU (not the benchmark line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -539,6 +568,8 @@ def main():
         return run_suite(args)
     if args.copies:
         return run_copies(args)
+    if args.rates:
+        return run_rates(args)
 
     import torch
     rank, world, local = rank_info()

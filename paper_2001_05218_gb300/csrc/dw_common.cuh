@@ -587,6 +587,16 @@ struct Spin<PDF> {
   __device__ static __forceinline__ void store(char* base, int vh, int s, const Cx<DF> (&v)[12]) {
     store_packed(base, vh, s, pack(v));
   }
+  // the three colours of one spin
+  __device__ static __forceinline__ void load_spin(const char* base, int vh, int s, int spin, Cx<DF> (&v)[3]) {
+    const float4* b = reinterpret_cast<const float4*>(base);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float4 t = __ldg(b + (size_t)(3 * spin + c) * vh + s);
+      v[c].re = df_make(t.x, t.y);
+      v[c].im = df_make(t.z, t.w);
+    }
+  }
   __device__ static __forceinline__ void roundtrip(Cx<DF> (&)[12]) {}
 };
 

@@ -323,6 +323,23 @@ __device__ __forceinline__ void project_rt(const DirSpin& d, const Cx<R> (&p)[12
     h[3 + c] = cadd_lazy(p[3 + c], mul_unit(q1, d.c1));
   }
 }
+// The same projection from a double-float field, loading for each half-spinor
+// row only the two spins it combines, so that six of the twelve components
+// are live at a time.
+template <class In>
+__device__ __forceinline__ void project_rt_loaded(const DirSpin& d, const In& in, const SysDesc& S, int par, int r,
+                                                  int n, Cx<DF> (&h)[6]) {
+  const char* base = slot_ptr(S, in.slot, r, par);
+  Cx<DF> a[3], q[3];
+  Spin<PDF>::load_spin(base, S.vh, n, 0, a);
+  Spin<PDF>::load_spin(base, S.vh, n, d.swap ? 3 : 2, q);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) h[c] = cadd_lazy(a[c], mul_unit(q[c], d.c0));
+  Spin<PDF>::load_spin(base, S.vh, n, 1, a);
+  Spin<PDF>::load_spin(base, S.vh, n, d.swap ? 2 : 3, q);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) h[3 + c] = cadd_lazy(a[c], mul_unit(q[c], d.c1));
+}
 // acc stays unnormalised across the eight directions (renormalised by the caller)
 template <typename R>
 __device__ __forceinline__ void accumulate_rt(const DirSpin& d, Cx<R> (&acc)[12], const Cx<R> (&g)[6]) {
@@ -823,11 +840,10 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
 #pragma unroll 1
         for (int mu = 0; mu < 4; ++mu) {
           float eta;
-          Cx<R> p[12], h[6], g[6], u[9];
+          Cx<R> h[6], g[6], u[9];
           const DirSpin df = dir_spin(mu, SF), db = dir_spin(mu, SB);
           const int nf = neighbour_rt(S, c, s, mu, +1, &eta);
-          in.load(S, pin, r, nf, p);
-          project_rt(df, p, h);
+          project_rt_loaded(df, in, S, pin, r, nf, h);
           Link<LP, C12>::load(ulink_own + mu * mu_stride, S.vh, s, u);
           if (eta < 0.f) {
 #pragma unroll
@@ -836,8 +852,7 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
           su3_mul<false>(u, h, g);
           accumulate_rt(df, acc, g);
           const int nb = neighbour_rt(S, c, s, mu, -1, &eta);
-          in.load(S, pin, r, nb, p);
-          project_rt(db, p, h);
+          project_rt_loaded(db, in, S, pin, r, nb, h);
           Link<LP, C12>::load(ulink_nb + mu * mu_stride, S.vh, nb, u);
           if (eta < 0.f) {
 #pragma unroll
