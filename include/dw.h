@@ -133,20 +133,28 @@ dw_status dw_field_mark_modified(dw_field* f);
 dw_status dw_field_free(dw_field* f);
 
 /* Copy host canonical complex128 data into the field (converted to the
- * field's storage precision and layout): one host-to-device copy into a
- * staging buffer, then the layout kernel, both on `stream`.  `host` may be
- * pageable or pinned; from pinned (page-locked) memory the copy is
- * asynchronous and the buffer must stay valid and unchanged until the stream
- * reaches this point.  Staging buffers come from a memory pool owned by the
- * library, which keeps up to 8 GiB per device reserved between calls. */
+ * field's storage precision and layout): host-to-device copies into a
+ * staging buffer, then the layout kernel; a gauge field's derived link copies
+ * (see dw_field_wrap) are refreshed by the same call.  Transfers of 64 MiB
+ * and more run in up to 8 chunks: the copies go on a copy stream owned by the
+ * library, the kernels on `stream`, so that the kernels of one chunk overlap
+ * the copy of the next; events order the copy stream after the work already
+ * on `stream` and `stream` after the copies, so the call is ordered on
+ * `stream` as one copy plus kernel would be.  (Under stream capture the call
+ * issues one copy and one kernel on `stream`.)  `host` may be pageable or
+ * pinned; from pinned (page-locked) memory the copies are asynchronous and the
+ * buffer must stay valid and unchanged until the stream reaches this point.
+ * Staging buffers come from a memory pool owned by the library, which keeps up
+ * to 8 GiB per device reserved between calls. */
 dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream);
 
 /* Copy the field back to host canonical complex128 (layout kernel into a
- * staging buffer, then one device-to-host copy).  Data are valid once
- * `stream` has been synchronised. */
+ * staging buffer, then device-to-host copies, chunked as in dw_field_upload).
+ * Data are valid once `stream` has been synchronised. */
 dw_status dw_field_download(const dw_field* f, double* host, dw_stream_t stream);
 
-/* As upload/download, with the canonical complex128 array in device memory. */
+/* As upload/download, with the canonical complex128 array in device memory
+ * (one layout kernel on `stream`; import also refreshes derived link copies). */
 dw_status dw_field_import(dw_field* f, const double* dev_canonical, dw_stream_t stream);
 dw_status dw_field_export(const dw_field* f, double* dev_canonical, dw_stream_t stream);
 

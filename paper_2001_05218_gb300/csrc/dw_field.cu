@@ -196,12 +196,17 @@ __host__ __device__ inline void site_to_eo(const int* d, long long lex, int* par
   *j = lex >> 1;
 }
 
+// Spinor kernels run over canonical elements e = rhs * nsite + site in
+// [e0, e1); gauge kernels over canonical sites [s0, s1).  A host transfer in
+// chunks launches one kernel per chunk.
 template <int P>
-__global__ void k_pack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, const double2* __restrict__ can,
-                              Slot dst) {
-  const long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void k_pack_spinor(Dims4 dm, int vh, int npar, int par0, long long e0, long long e1,
+                              const double2* __restrict__ can, Slot dst) {
+  const long long e = e0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= e1) return;
   const long long nsite = (long long)vh * npar;
-  if (site >= nsite) return;
+  const int r = (int)(e / nsite);
+  const long long site = e - r * nsite;
   int par = par0, pi = 0;
   long long j = site;
   if (npar == 2) {
@@ -209,23 +214,24 @@ __global__ void k_pack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, co
     pi = par;
   }
   using R = typename Spin<P>::R;
-  for (int r = 0; r < nrhs; ++r) {
-    const double2* src = can + ((long long)r * nsite + site) * 12;
-    Cx<R> v[12];
+  const double2* src = can + e * 12;
+  Cx<R> v[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      double2 t = src[k];
-      v[k] = cx((R)t.x, (R)t.y);
-    }
-    Spin<P>::store(dst.p + r * dst.rhs_stride + pi * dst.par_stride, vh, (int)j, v);
+  for (int k = 0; k < 12; ++k) {
+    double2 t = src[k];
+    v[k] = cx((R)t.x, (R)t.y);
   }
+  Spin<P>::store(dst.p + r * dst.rhs_stride + pi * dst.par_stride, vh, (int)j, v);
 }
 
 template <int P>
-__global__ void k_unpack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, Slot srcs, double2* __restrict__ can) {
-  const long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void k_unpack_spinor(Dims4 dm, int vh, int npar, int par0, long long e0, long long e1, Slot srcs,
+                                double2* __restrict__ can) {
+  const long long e = e0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (e >= e1) return;
   const long long nsite = (long long)vh * npar;
-  if (site >= nsite) return;
+  const int r = (int)(e / nsite);
+  const long long site = e - r * nsite;
   int par = par0, pi = 0;
   long long j = site;
   if (npar == 2) {
@@ -233,19 +239,18 @@ __global__ void k_unpack_spinor(Dims4 dm, int vh, int nrhs, int npar, int par0, 
     pi = par;
   }
   using R = typename Spin<P>::R;
-  for (int r = 0; r < nrhs; ++r) {
-    Cx<R> v[12];
-    Spin<P>::load(srcs.p + r * srcs.rhs_stride + pi * srcs.par_stride, vh, (int)j, v);
-    double2* o = can + ((long long)r * nsite + site) * 12;
+  Cx<R> v[12];
+  Spin<P>::load(srcs.p + r * srcs.rhs_stride + pi * srcs.par_stride, vh, (int)j, v);
+  double2* o = can + e * 12;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) o[k] = make_double2((double)v[k].re, (double)v[k].im);
-  }
+  for (int k = 0; k < 12; ++k) o[k] = make_double2((double)v[k].re, (double)v[k].im);
 }
 
 template <int P, bool C12>
-__global__ void k_pack_gauge(Dims4 dm, int vh, const double2* __restrict__ can, char* dst) {
-  const long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (site >= 2ll * vh) return;
+__global__ void k_pack_gauge(Dims4 dm, int vh, long long s0, long long s1, const double2* __restrict__ can,
+                             char* dst) {
+  const long long site = s0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (site >= s1) return;
   int par;
   long long j;
   site_to_eo(dm.d, site, &par, &j);
@@ -264,9 +269,10 @@ __global__ void k_pack_gauge(Dims4 dm, int vh, const double2* __restrict__ can, 
 }
 
 template <int P, bool C12>
-__global__ void k_unpack_gauge(Dims4 dm, int vh, const char* src, double2* __restrict__ can) {
-  const long long site = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (site >= 2ll * vh) return;
+__global__ void k_unpack_gauge(Dims4 dm, int vh, long long s0, long long s1, const char* src,
+                               double2* __restrict__ can) {
+  const long long site = s0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (site >= s1) return;
   int par;
   long long j;
   site_to_eo(dm.d, site, &par, &j);
@@ -281,12 +287,13 @@ __global__ void k_unpack_gauge(Dims4 dm, int vh, const char* src, double2* __res
   }
 }
 
-// FP64 18-real links -> (P, C12) storage
+// FP64 18-real links -> (P, C12) storage, checkerboard indexes [j0, j1) of
+// all eight (parity, mu) planes
 template <int P, bool C12>
-__global__ void k_convert_gauge(int vh, const char* src, char* dst) {
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__global__ void k_convert_gauge(int vh, long long j0, long long j1, const char* src, char* dst) {
+  const long long j = j0 + blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int pm = blockIdx.y;  // parity*4 + mu
-  if (j >= vh) return;
+  if (j >= j1) return;
   const long long lsrc = (long long)Link<P64, false>::kBytes * vh;
   const long long ldst = (long long)Link<P, C12>::kBytes * vh;
   Cx<double> u[9];
@@ -314,54 +321,81 @@ static Dims4 dims4(const dw_lattice& l) {
     case DW_I16: { constexpr int PP = PI16; BODY; } break; \
   }
 
-dw_status pack_spinor_from_canonical(dw_field* f, const double* dev, cudaStream_t st) {
-  const int vh = (int)vh_of(f->lat);
-  const int npar = npar_of(f->kind);
-  const int par0 = f->kind == DW_SPINOR_ODD ? 1 : 0;
-  dim3 b(256), g((unsigned)(((long long)vh * npar + 255) / 256));
-  Slot s = spinor_slot(f);
-  const double2* c = reinterpret_cast<const double2*>(dev);
-  DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_spinor<PP><<<g, b, 0, st>>>(dims4(f->lat), vh, f->nrhs, npar, par0, c, s)));
-  DW_CUDA(cudaGetLastError());
-  return DW_OK;
+static unsigned blocks_for(long long n) { return (unsigned)((n + 255) / 256); }
+
+long long canonical_units(const dw_field* f) {
+  const long long vh = vh_of(f->lat);
+  if (f->kind == DW_GAUGE) return 2 * vh;
+  return (long long)f->nrhs * vh * npar_of(f->kind);
 }
 
-dw_status unpack_spinor_to_canonical(const dw_field* f, double* dev, cudaStream_t st) {
-  const int vh = (int)vh_of(f->lat);
-  const int npar = npar_of(f->kind);
-  const int par0 = f->kind == DW_SPINOR_ODD ? 1 : 0;
-  dim3 b(256), g((unsigned)(((long long)vh * npar + 255) / 256));
-  Slot s = spinor_slot(f);
-  double2* c = reinterpret_cast<double2*>(dev);
-  DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_spinor<PP><<<g, b, 0, st>>>(dims4(f->lat), vh, f->nrhs, npar, par0, s, c)));
-  DW_CUDA(cudaGetLastError());
-  return DW_OK;
-}
+size_t canonical_unit_bytes(const dw_field* f) { return f->kind == DW_GAUGE ? 4 * 9 * 16 : 12 * 16; }
 
-static dw_status pack_gauge(dw_field* f, const double* dev, cudaStream_t st) {
+dw_status pack_range(dw_field* f, const double* can, long long u0, long long u1, cudaStream_t st) {
+  if (u1 <= u0) return DW_OK;
   const int vh = (int)vh_of(f->lat);
-  dim3 b(256), g((unsigned)((2ll * vh + 255) / 256));
-  const double2* c = reinterpret_cast<const double2*>(dev);
-  if (f->compress12) {
-    DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_gauge<PP, true><<<g, b, 0, st>>>(dims4(f->lat), vh, c, f->ptr)));
+  const double2* c = reinterpret_cast<const double2*>(can);
+  dim3 b(256), g(blocks_for(u1 - u0));
+  if (f->kind == DW_GAUGE) {
+    if (f->compress12) {
+      DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_gauge<PP, true><<<g, b, 0, st>>>(dims4(f->lat), vh, u0, u1, c, f->ptr)));
+    } else {
+      DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_gauge<PP, false><<<g, b, 0, st>>>(dims4(f->lat), vh, u0, u1, c, f->ptr)));
+    }
   } else {
-    DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_gauge<PP, false><<<g, b, 0, st>>>(dims4(f->lat), vh, c, f->ptr)));
+    const int npar = npar_of(f->kind);
+    const int par0 = f->kind == DW_SPINOR_ODD ? 1 : 0;
+    Slot s = spinor_slot(f);
+    DW_PREC_DISPATCH(f->prec, (count_launch(), k_pack_spinor<PP><<<g, b, 0, st>>>(dims4(f->lat), vh, npar, par0, u0, u1, c, s)));
   }
   DW_CUDA(cudaGetLastError());
   return DW_OK;
 }
 
-static dw_status unpack_gauge(const dw_field* f, double* dev, cudaStream_t st) {
+dw_status unpack_range(const dw_field* f, double* can, long long u0, long long u1, cudaStream_t st) {
+  if (u1 <= u0) return DW_OK;
   const int vh = (int)vh_of(f->lat);
-  dim3 b(256), g((unsigned)((2ll * vh + 255) / 256));
-  double2* c = reinterpret_cast<double2*>(dev);
-  if (f->compress12) {
-    DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_gauge<PP, true><<<g, b, 0, st>>>(dims4(f->lat), vh, f->ptr, c)));
+  double2* c = reinterpret_cast<double2*>(can);
+  dim3 b(256), g(blocks_for(u1 - u0));
+  if (f->kind == DW_GAUGE) {
+    if (f->compress12) {
+      DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_gauge<PP, true><<<g, b, 0, st>>>(dims4(f->lat), vh, u0, u1, f->ptr, c)));
+    } else {
+      DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_gauge<PP, false><<<g, b, 0, st>>>(dims4(f->lat), vh, u0, u1, f->ptr, c)));
+    }
   } else {
-    DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_gauge<PP, false><<<g, b, 0, st>>>(dims4(f->lat), vh, f->ptr, c)));
+    const int npar = npar_of(f->kind);
+    const int par0 = f->kind == DW_SPINOR_ODD ? 1 : 0;
+    Slot s = spinor_slot(f);
+    DW_PREC_DISPATCH(f->prec, (count_launch(), k_unpack_spinor<PP><<<g, b, 0, st>>>(dims4(f->lat), vh, npar, par0, u0, u1, s, c)));
   }
   DW_CUDA(cudaGetLastError());
   return DW_OK;
+}
+
+static dw_status convert_links(const dw_field* U, const dw_field::Derived& d, long long j0, long long j1,
+                               cudaStream_t st) {
+  if (j1 <= j0) return DW_OK;
+  const int vh = (int)vh_of(U->lat);
+  dim3 b(256), g(blocks_for(j1 - j0), 8);
+  if (d.c12) {
+    DW_PREC_DISPATCH(d.prec, (count_launch(), k_convert_gauge<PP, true><<<g, b, 0, st>>>(vh, j0, j1, U->ptr, d.ptr)));
+  } else {
+    DW_PREC_DISPATCH(d.prec, (count_launch(), k_convert_gauge<PP, false><<<g, b, 0, st>>>(vh, j0, j1, U->ptr, d.ptr)));
+  }
+  DW_CUDA(cudaGetLastError());
+  return DW_OK;
+}
+
+dw_status refresh_derived_range(dw_field* U, long long s0, long long s1, cudaStream_t st) {
+  if (U->kind != DW_GAUGE) return DW_OK;
+  // lexicographic sites 2j and 2j+1 are the two parities of checkerboard index j
+  for (auto& d : U->derived) DW_TRY(convert_links(U, d, s0 / 2, (s1 + 1) / 2, st));
+  return DW_OK;
+}
+
+void mark_derived_current(dw_field* U) {
+  for (auto& d : U->derived) d.version = U->version;
 }
 
 dw_status derived_links(dw_field* U, int prec, int c12, cudaStream_t st, const char** out) {
@@ -374,14 +408,7 @@ dw_status derived_links(dw_field* U, int prec, int c12, cudaStream_t st, const c
   for (auto& d : U->derived)
     if (d.prec == prec && d.c12 == c12) {
       if (d.version != U->version) {
-        const int vh = (int)vh_of(U->lat);
-        dim3 b(256), g((vh + 255) / 256, 8);
-        if (c12) {
-          DW_PREC_DISPATCH(prec, (count_launch(), k_convert_gauge<PP, true><<<g, b, 0, st>>>(vh, U->ptr, d.ptr)));
-        } else {
-          DW_PREC_DISPATCH(prec, (count_launch(), k_convert_gauge<PP, false><<<g, b, 0, st>>>(vh, U->ptr, d.ptr)));
-        }
-        DW_CUDA(cudaGetLastError());
+        DW_TRY(convert_links(U, d, 0, vh_of(U->lat), st));
         d.version = U->version;
       }
       *out = d.ptr;
@@ -642,25 +669,20 @@ dw_status dw_field_info(const dw_field* f, dw_lattice* lat, dw_kind* kind, dw_pr
   return DW_OK;
 }
 
-static size_t canonical_bytes(const dw_field* f) {
-  const long long V = volume_of(f->lat);
-  if (f->kind == DW_GAUGE) return (size_t)V * 4 * 9 * 16;
-  return (size_t)f->nrhs * (f->kind == DW_SPINOR_FULL ? V : V / 2) * 12 * 16;
-}
-
 dw_status dw_field_import(dw_field* f, const double* dev, dw_stream_t stream) {
   DW_CHECK(f != nullptr && dev != nullptr, DW_ERR_ARG, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   f->version += 1;
-  if (f->kind == DW_GAUGE) return pack_gauge(f, dev, st);
-  return pack_spinor_from_canonical(f, dev, st);
+  const long long nu = canonical_units(f);
+  DW_TRY(pack_range(f, dev, 0, nu, st));
+  DW_TRY(refresh_derived_range(f, 0, nu, st));
+  mark_derived_current(f);
+  return DW_OK;
 }
 
 dw_status dw_field_export(const dw_field* f, double* dev, dw_stream_t stream) {
   DW_CHECK(f != nullptr && dev != nullptr, DW_ERR_ARG, "NULL argument");
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (f->kind == DW_GAUGE) return unpack_gauge(f, dev, st);
-  return unpack_spinor_to_canonical(f, dev, st);
+  return unpack_range(f, dev, 0, canonical_units(f), reinterpret_cast<cudaStream_t>(stream));
 }
 
 // Staging buffers for host transfers come from a stream-ordered memory pool
@@ -691,20 +713,95 @@ static dw_status staging_pool(cudaMemPool_t* out) {
   return DW_OK;
 }
 
+// Large host transfers run in chunks: the DMA copies go on a copy stream owned
+// by the library (one per device) and the layout kernels on the caller's
+// stream, so that the kernels of one chunk run under the copy of the next.
+// Events order the two streams both ways, which keeps the call ordered on the
+// caller's stream exactly as a single copy plus kernel would be.
+static constexpr int kMaxChunks = 8;
+static constexpr size_t kChunkMinBytes = 32ull << 20;
+struct CopyLane {
+  cudaStream_t s = nullptr;
+  cudaEvent_t ev[kMaxChunks + 1] = {};
+};
+static std::mutex g_lane_mu;  // held while a transfer enqueues (the events are reused)
+static CopyLane g_lane[64];
+
+static dw_status copy_lane(CopyLane** out) {
+  int dev = 0;
+  DW_CUDA(cudaGetDevice(&dev));
+  DW_CHECK(dev >= 0 && dev < 64, DW_ERR_ARG, "device index %d out of range", dev);
+  CopyLane& l = g_lane[dev];
+  if (!l.s) {
+    DW_CUDA(cudaStreamCreateWithFlags(&l.s, cudaStreamNonBlocking));
+    for (auto& e : l.ev) DW_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  *out = &l;
+  return DW_OK;
+}
+
+// Number of chunks for a transfer of nb bytes on stream st: one (a single copy
+// and kernel on st) for small transfers and while st is being captured.
+static int transfer_chunks(size_t nb, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return 1;
+  const size_t n = nb / kChunkMinBytes;
+  return n < 2 ? 1 : (int)(n < (size_t)kMaxChunks ? n : kMaxChunks);
+}
+
+// First canonical unit of chunk k of n (gauge fields: an even site, so that a
+// chunk holds both parities of each of its checkerboard indexes)
+static long long chunk_start(const dw_field* f, long long nu, int k, int n) {
+  long long u = nu * k / n;
+  if (f->kind == DW_GAUGE) u &= ~1ll;
+  return u;
+}
+
 dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream) {
   DW_CHECK(f != nullptr && host != nullptr, DW_ERR_ARG, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // one DMA copy into a device staging buffer, then the layout kernel on the
-  // device (measured on a Grace-Blackwell node: about 200 GB/s from pinned
-  // memory, against about 140 GB/s for a kernel reading host memory directly)
-  const size_t nb = canonical_bytes(f);
+  // DMA copies into a device staging buffer, then the layout kernel (and the
+  // refresh of derived link copies) on the device (measured on a
+  // Grace-Blackwell node: about 200 GB/s from pinned memory, against about
+  // 140 GB/s for a kernel reading host memory directly)
+  const long long nu = canonical_units(f);
+  const size_t ub = canonical_unit_bytes(f);
+  const size_t nb = (size_t)nu * ub;
   cudaMemPool_t pool;
   DW_TRY(staging_pool(&pool));
-  void* tmp = nullptr;
-  DW_CUDA(cudaMallocFromPoolAsync(&tmp, nb, pool, st));
-  cudaError_t e = cudaMemcpyAsync(tmp, host, nb, cudaMemcpyHostToDevice, st);
-  dw_status s = e == cudaSuccess ? dw_field_import(f, static_cast<const double*>(tmp), stream)
-                                 : cuda_error(e, "cudaMemcpyAsync(host to device)", __FILE__, __LINE__);
+  char* tmp = nullptr;
+  DW_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&tmp), nb, pool, st));
+  const char* h = reinterpret_cast<const char*>(host);
+  f->version += 1;
+  const int n = transfer_chunks(nb, st);
+  dw_status s = DW_OK;
+  if (n == 1) {
+    cudaError_t e = cudaMemcpyAsync(tmp, h, nb, cudaMemcpyHostToDevice, st);
+    s = e == cudaSuccess ? pack_range(f, reinterpret_cast<const double*>(tmp), 0, nu, st)
+                         : cuda_error(e, "cudaMemcpyAsync(host to device)", __FILE__, __LINE__);
+    if (s == DW_OK) s = refresh_derived_range(f, 0, nu, st);
+  } else {
+    std::lock_guard<std::mutex> lock(g_lane_mu);
+    CopyLane* l = nullptr;
+    s = copy_lane(&l);
+    cudaError_t e = cudaSuccess;
+    if (s == DW_OK) e = cudaEventRecord(l->ev[0], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(l->s, l->ev[0], 0);
+    for (int k = 0; k < n && s == DW_OK && e == cudaSuccess; ++k) {
+      const long long u0 = chunk_start(f, nu, k, n), u1 = chunk_start(f, nu, k + 1, n);
+      e = cudaMemcpyAsync(tmp + u0 * ub, h + u0 * ub, (u1 - u0) * ub, cudaMemcpyHostToDevice, l->s);
+      if (e == cudaSuccess) e = cudaEventRecord(l->ev[k + 1], l->s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, l->ev[k + 1], 0);
+      if (e == cudaSuccess) s = pack_range(f, reinterpret_cast<const double*>(tmp), u0, u1, st);
+      if (e == cudaSuccess && s == DW_OK) s = refresh_derived_range(f, u0, u1, st);
+    }
+    if (l != nullptr && (s != DW_OK || e != cudaSuccess)) {
+      // an error part way: the staging buffer's release still waits for the copies issued
+      if (cudaEventRecord(l->ev[kMaxChunks], l->s) == cudaSuccess) cudaStreamWaitEvent(st, l->ev[kMaxChunks], 0);
+    }
+    if (s == DW_OK && e != cudaSuccess) s = cuda_error(e, "chunked host-to-device copy", __FILE__, __LINE__);
+  }
+  if (s == DW_OK) mark_derived_current(f);
   cudaFreeAsync(tmp, st);
   return s;
 }
@@ -712,17 +809,46 @@ dw_status dw_field_upload(dw_field* f, const double* host, dw_stream_t stream) {
 dw_status dw_field_download(const dw_field* f, double* host, dw_stream_t stream) {
   DW_CHECK(f != nullptr && host != nullptr, DW_ERR_ARG, "NULL argument");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // layout kernel into a device staging buffer, then one DMA copy (kernel
+  // layout kernel into a device staging buffer, then DMA copies (kernel
   // writes into host memory reach only about a quarter of the DMA rate)
-  const size_t nb = canonical_bytes(f);
+  const long long nu = canonical_units(f);
+  const size_t ub = canonical_unit_bytes(f);
+  const size_t nb = (size_t)nu * ub;
   cudaMemPool_t pool;
   DW_TRY(staging_pool(&pool));
-  void* tmp = nullptr;
-  DW_CUDA(cudaMallocFromPoolAsync(&tmp, nb, pool, st));
-  dw_status s = dw_field_export(f, static_cast<double*>(tmp), stream);
-  if (s == DW_OK) {
-    cudaError_t e = cudaMemcpyAsync(host, tmp, nb, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) s = cuda_error(e, "cudaMemcpyAsync(device to host)", __FILE__, __LINE__);
+  char* tmp = nullptr;
+  DW_CUDA(cudaMallocFromPoolAsync(reinterpret_cast<void**>(&tmp), nb, pool, st));
+  char* h = reinterpret_cast<char*>(host);
+  const int n = transfer_chunks(nb, st);
+  dw_status s = DW_OK;
+  if (n == 1) {
+    s = unpack_range(f, reinterpret_cast<double*>(tmp), 0, nu, st);
+    if (s == DW_OK) {
+      cudaError_t e = cudaMemcpyAsync(h, tmp, nb, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) s = cuda_error(e, "cudaMemcpyAsync(device to host)", __FILE__, __LINE__);
+    }
+  } else {
+    std::lock_guard<std::mutex> lock(g_lane_mu);
+    CopyLane* l = nullptr;
+    s = copy_lane(&l);
+    cudaError_t e = cudaSuccess;
+    int issued = 0;  // chunks whose copy is on the copy stream
+    for (int k = 0; k < n && s == DW_OK && e == cudaSuccess; ++k) {
+      const long long u0 = chunk_start(f, nu, k, n), u1 = chunk_start(f, nu, k + 1, n);
+      s = unpack_range(f, reinterpret_cast<double*>(tmp), u0, u1, st);
+      if (s != DW_OK) break;
+      e = cudaEventRecord(l->ev[k], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(l->s, l->ev[k], 0);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(h + u0 * ub, tmp + u0 * ub, (u1 - u0) * ub, cudaMemcpyDeviceToHost, l->s);
+      if (e == cudaSuccess) issued = k + 1;
+    }
+    // the caller's stream (and the staging buffer's release) waits for every copy issued
+    if (issued > 0) {
+      cudaError_t e2 = cudaEventRecord(l->ev[kMaxChunks], l->s);
+      if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, l->ev[kMaxChunks], 0);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (s == DW_OK && e != cudaSuccess) s = cuda_error(e, "chunked device-to-host copy", __FILE__, __LINE__);
   }
   cudaFreeAsync(tmp, st);
   return s;

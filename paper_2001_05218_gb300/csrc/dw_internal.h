@@ -111,7 +111,16 @@ struct RedBuf {
 // Gauge field copy in (prec, c12) storage, cached on the handle.
 dw_status derived_links(dw_field* U, int prec, int c12, cudaStream_t st, const char** out);
 
-dw_status pack_spinor_from_canonical(dw_field* f, const double* dev, cudaStream_t st);
-dw_status unpack_spinor_to_canonical(const dw_field* f, double* dev, cudaStream_t st);
+// Canonical layout <-> storage over a range of canonical units: sites for
+// gauge fields, (rhs, site) pairs for spinor fields (canonical_units of them,
+// canonical_unit_bytes each).  can points at unit 0 of the canonical array.
+long long canonical_units(const dw_field* f);
+size_t canonical_unit_bytes(const dw_field* f);
+dw_status pack_range(dw_field* f, const double* can, long long u0, long long u1, cudaStream_t st);
+dw_status unpack_range(const dw_field* f, double* can, long long u0, long long u1, cudaStream_t st);
+// Gauge fields: converts the derived link copies over canonical sites [s0, s1)
+// (s0 even); mark_derived_current then records them as up to date.
+dw_status refresh_derived_range(dw_field* U, long long s0, long long s1, cudaStream_t st);
+void mark_derived_current(dw_field* U);
 
 }  // namespace dw
