@@ -299,7 +299,9 @@ def run_copies(args):
     x down) with plain PyTorch copies between page-locked host memory and
     device memory, each synchronised and timed on the host; no library call.
     Shows the platform's copy rate per step, including its occasional slow
-    steps.  Not the benchmark line."""
+    steps, the same copies split over several streams, and DMA against SM
+    kernels that access the page-locked memory directly (alone and together).
+    Not the benchmark line."""
     import torch
     torch.cuda.set_device(0)
     from paper_2001_05218_gb300 import inputs as I
@@ -356,6 +358,44 @@ def run_copies(args):
         split[str(k)] = {"median_ms": m.round(3).tolist(),
                          "median_gbs": (gb[[0, 2]] / (m / 1e3)).round(1).tolist()}
     out["split_streams"] = split
+
+    # DMA against an SM kernel reading / writing the page-locked buffer through
+    # its device address (a tensor aliasing it), alone and together on two
+    # streams over disjoint parts (fraction f by DMA)
+    class _HostView:
+        def __init__(self, h):
+            self.__cuda_array_interface__ = {"shape": (h.numel(),), "typestr": "<f8", "data": (h.data_ptr(), False),
+                                             "version": 3}
+
+    Uv = torch.as_tensor(_HostView(Uh), device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def med_gbs(fn):
+        ts = [t(fn) for _ in range(args.warmup + max(3, args.steps // 4))][args.warmup:]
+        return round(gb[0] / (float(np.median(ts)) / 1e3), 1)
+
+    def both(f, up):
+        k = int(nU * f)
+        cur = torch.cuda.current_stream()
+        for st_ in (s1, s2):
+            st_.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            (Ud[:k].copy_(Uh[:k], non_blocking=True) if up else Uh[:k].copy_(Ud[:k], non_blocking=True))
+        with torch.cuda.stream(s2):
+            (torch.add(Uv[k:], 0.0, out=Ud[k:]) if up else torch.add(Ud[k:], 0.0, out=Uv[k:]))
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    dma_sm = {"bytes": int(gb[0] * 1e9),
+              "h2d": {"dma": med_gbs(lambda: Ud.copy_(Uh, non_blocking=True)),
+                      "sm": med_gbs(lambda: torch.add(Uv, 0.0, out=Ud))},
+              "d2h": {"dma": med_gbs(lambda: Uh.copy_(Ud, non_blocking=True)),
+                      "sm": med_gbs(lambda: torch.add(Ud, 0.0, out=Uv))}}
+    for f in (0.5, 0.6, 0.7, 0.8, 0.9):
+        dma_sm["h2d"]["both_f%.1f" % f] = med_gbs(lambda: both(f, True))
+        dma_sm["d2h"]["both_f%.1f" % f] = med_gbs(lambda: both(f, False))
+    torch.cuda.synchronize()
+    out["dma_vs_sm_gbs"] = dma_sm
     print(json.dumps(out))
 
 

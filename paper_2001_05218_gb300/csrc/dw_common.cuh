@@ -860,7 +860,9 @@ struct Batch {
   int nsys;  // systems in this launch
   int ntot;  // blocks per parity over all systems (grid x per parity)
   int T;     // sites per block (per right-hand side), multiple of 32
-  int RB;    // right-hand sides per block (grid y = ceil(nrhs / RB))
+  int RB;    // right-hand sides per block
+  int ny;    // right-hand-side blocks, ceil(nrhs / RB): the grid is x = (parity
+             // range, tile, rhs block) with the rhs block varying fastest
   SysDesc sd[kMaxSys];
 };
 
@@ -1069,9 +1071,9 @@ __device__ __forceinline__ DF warp_sum_lane0(DF v) {
 }
 
 // Deterministic grid reduction in two kernels.  A block holds RB groups of T
-// threads (T a multiple of 32); group g works on right-hand side
-// r = blockIdx.y*RB + g.  The producing kernel sums each group's values in a
-// fixed order (double-float on the FP32 pipes, or IEEE FP64 for FP64
+// threads (T a multiple of 32); group g works on right-hand side r = y*RB + g
+// for the block's right-hand-side block y.  The producing kernel sums each
+// group's values in a fixed order (double-float on the FP32 pipes, or IEEE FP64 for FP64
 // arithmetic) and writes one IEEE-FP64 partial per block and right-hand side;
 // nothing in it waits.  k_finish, launched next on the same stream (which
 // orders the partial writes before it), sums each column's partials in a

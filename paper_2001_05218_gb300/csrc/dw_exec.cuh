@@ -118,8 +118,8 @@ inline void hop(const Exec& E, int par_mode, int link_slot, In in, Epi epi, int 
   bool launched = false;
   if constexpr ((SPA == P16 || SPA == PB16) && LP == SPA && OP == OP_WILSON && std::is_same<In, InOne<SPA>>::value) {
     if (E.P.pair && E.P.nrhs >= 2) {  // two right-hand sides per thread, each link loaded once for both
-      dim3 g = E.grid(par_mode);
-      g.y = (E.P.nrhs + 2 * E.P.B.RB - 1) / (2 * E.P.B.RB);
+      const unsigned npar = par_mode == 2 ? 2u : 1u;
+      const dim3 g(npar * E.P.B.ntot * ((E.P.nrhs + 2 * E.P.B.RB - 1) / (2 * E.P.B.RB)));
       k_hop_pair<SPA, C12, DAG, Epi><<<g, E.P.block, 0, E.st>>>(E.P.B, par_mode, link_slot, in.slot, epi, E.ra(fin));
       launched = true;
     }

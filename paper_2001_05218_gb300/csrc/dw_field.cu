@@ -160,8 +160,9 @@ void make_plan(Plan& P, const dw_lattice* lats, int n, int nrhs, int T, int RB) 
   P.partials = part;
   const int gy = (nrhs + RB - 1) / RB;
   P.block = dim3(T * RB);
-  P.grid1 = dim3(tile, gy);
-  P.grid2 = dim3(2 * tile, gy);
+  P.B.ny = gy;
+  P.grid1 = dim3(tile * gy);
+  P.grid2 = dim3(2 * tile * gy);
 }
 
 // ------------------------------------------------------------------ layout kernels

@@ -644,7 +644,10 @@ struct EpiResidFull {
   __shared__ SysDesc S;                                                    \
   __shared__ int act[64];                                                  \
   const int T = B.T, RB = B.RB;                                            \
-  int b = blockIdx.x, par;                                                 \
+  /* the right-hand-side block varies fastest: the blocks of one tile run  \
+     together and share its links and neighbours in L2 */                  \
+  const int by = (int)(blockIdx.x % (unsigned)B.ny);                        \
+  int b = (int)(blockIdx.x / (unsigned)B.ny), par;                         \
   if (par_mode == 2) {                                                     \
     par = b >= B.ntot ? 1 : 0;                                             \
     b -= par * B.ntot;                                                     \
@@ -660,7 +663,7 @@ struct EpiResidFull {
   for (int i_ = 0; i_ < S.nrhs; ++i_) any |= act[i_];                      \
   if (!any) return;                                                        \
   const int rl = threadIdx.x / T;                                          \
-  const int r = blockIdx.y * RB + rl;                                      \
+  const int r = by * RB + rl;                                              \
   const int tile = b - S.tile0;                                            \
   const int s = tile * T + (threadIdx.x - rl * T);                         \
   const bool valid = s < S.vh && r < S.nrhs && act[r < S.nrhs ? r : 0];
@@ -669,7 +672,7 @@ struct EpiResidFull {
   {                                                                        \
     const int ntiles = par_mode == 2 ? 2 * S.tpp : S.tpp;                  \
     const int tt = par_mode == 2 ? par * S.tpp + tile : tile;              \
-    reduce_block(S, T, RB, tt, ntiles, val, ra, blockIdx.y);               \
+    reduce_block(S, T, RB, tt, ntiles, val, ra, by);               \
   }
 // As DW_BLOCK_REDUCE, with the output stores STORE (a lambda) run after the
 // block's partial sums are written.
@@ -677,7 +680,7 @@ struct EpiResidFull {
   {                                                                        \
     const int ntiles = par_mode == 2 ? 2 * S.tpp : S.tpp;                  \
     const int tt = par_mode == 2 ? par * S.tpp + tile : tile;              \
-    reduce_block(S, T, RB, tt, ntiles, val, ra, blockIdx.y, STORE);        \
+    reduce_block(S, T, RB, tt, ntiles, val, ra, by, STORE);        \
   }
 
 // ------------------------------------------------------------------ the Laplacian's directions
@@ -887,8 +890,9 @@ __global__ void __launch_bounds__(256, HopOccupancy<SPA>::kMinBlocks)
 // 16-bit stencil with two right-hand sides per thread: each link is loaded,
 // and with 12-real compression its third row rebuilt, once and applied to
 // both; the two neighbour loads of a direction are in flight together.  Block:
-// T sites x RB thread groups, group g of grid row y taking right-hand sides
-// 2(y RB + g) and 2(y RB + g) + 1; grid.y = ceil(nrhs / (2 RB)).
+// T sites x RB thread groups, group g of right-hand-side block y taking
+// right-hand sides 2(y RB + g) and 2(y RB + g) + 1, for ny = ceil(nrhs / (2 RB))
+// blocks y; the grid is one-dimensional with y varying fastest.
 template <int SPA, bool C12, bool DAG, class Epi>
 __global__ void __launch_bounds__(256, 2)
     k_hop_pair(const __grid_constant__ Batch B, int par_mode, int link_slot, int in_slot, Epi epi, RedArgs ra) {
@@ -896,7 +900,9 @@ __global__ void __launch_bounds__(256, 2)
   __shared__ SysDesc S;
   __shared__ int act[64];
   const int T = B.T, RB = B.RB;
-  int b = blockIdx.x, par;
+  const unsigned ny = (unsigned)((B.sd[0].nrhs + 2 * RB - 1) / (2 * RB));
+  const int by = (int)(blockIdx.x % ny);
+  int b = (int)(blockIdx.x / ny), par;
   if (par_mode == 2) {
     par = b >= B.ntot ? 1 : 0;
     b -= par * B.ntot;
@@ -911,7 +917,7 @@ __global__ void __launch_bounds__(256, 2)
   for (int i_ = 0; i_ < S.nrhs; ++i_) any |= act[i_];
   if (!any) return;
   const int rl = threadIdx.x / T;
-  const int r0 = (blockIdx.y * RB + rl) * 2, r1 = r0 + 1;
+  const int r0 = (by * RB + rl) * 2, r1 = r0 + 1;
   const int tile = b - S.tile0;
   const int s = tile * T + (threadIdx.x - rl * T);
   const bool site = s < S.vh;
@@ -974,7 +980,7 @@ __global__ void __launch_bounds__(256, 2)
   if constexpr (Epi::kReduce) {
     const int ntiles = par_mode == 2 ? 2 * S.tpp : S.tpp;
     const int tt = par_mode == 2 ? par * S.tpp + tile : tile;
-    reduce_block_n<2>(S, T, RB, tt, ntiles, nrm, ra, blockIdx.y, [&] {
+    reduce_block_n<2>(S, T, RB, tt, ntiles, nrm, ra, by, [&] {
       if constexpr (Epi::kSplit) {
         if (v0) epi.commit(S, par, r0, s, po0);
         if (v1) epi.commit(S, par, r1, s, po1);
