@@ -574,6 +574,53 @@ def run_suite(args):
 
 
 # ---------------------------------------------------------------------- our arm
+def run_multi(args):
+    """The 12-source workload: 12 spin-colour point sources on 24^3x48 in one
+    multi-RHS solve, against one of them solved alone (x12).  Each solve runs
+    once as a graph after a warm-up (CUDA events, median of --steps), then once
+    host-stepped with CUDA events around every stencil launch (the per-kernel
+    split).  Not the benchmark line."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2001_05218_gb300 import dw
+    from paper_2001_05218_gb300 import inputs as I
+    name = "wilson_24x24x24x48_exp0.4_12src"
+    dims, kappa, U, _ = I.make_workload(name, with_source=False)
+    srcs = np.stack([I.point_source(dims, s_, c_) for s_ in range(4) for c_ in range(3)])
+    Ug = dw.gauge(dims, kappa, U)
+    p = dw.params(tol=1e-10, inner=args.inner or "f16", compress12=1 if args.compress12 is None else args.compress12,
+                  outer=args.outer, maxiter=100000)
+    st = torch.cuda.current_stream()
+    out = {"mode": "multi", "workload": name, "inner": args.inner or "f16", "outer": args.outer}
+    for nr in (12, 1):
+        bg = dw.spinor(dims, srcs if nr == 12 else srcs[0], nrhs=nr)
+        xg = dw.spinor(dims, nrhs=nr)
+        ts = []
+        for k in range(max(1, args.warmup) + max(1, args.steps)):
+            xg.storage.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, stt = dw.cg_solve(Ug, bg, xg, p)
+            e1.record(st)
+            torch.cuda.synchronize()
+            if k >= max(1, args.warmup):
+                ts.append(e0.elapsed_time(e1))
+        xg.storage.zero_()
+        torch.cuda.synchronize()
+        dw.profile_start(time_stencils=True)
+        dw.cg_solve(Ug, bg, xg, p)
+        prof, launches = dw.profile_stop()
+        out["rhs%d" % nr] = {"ms_median": float(np.median(ts)), "ms": [round(t, 3) for t in ts],
+                             "iters": [x["iters"] for x in stt],
+                             "reliable_updates": [x["reliable_updates"] for x in stt],
+                             "true_rel_resid_max": max(x["true_rel_resid"] for x in stt),
+                             "host_stepped": {"launches": launches,
+                                              "kernels": {k: {"launches": v["launches"], "ms": round(v["total_ms"], 3)}
+                                                          for k, v in prof.items()}}}
+    out["speedup_vs_12_single"] = 12 * out["rhs1"]["ms_median"] / out["rhs12"]["ms_median"]
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -599,6 +646,8 @@ def main():
     ap.add_argument("--suite", action="store_true", help="time every workload configuration (not the benchmark line)")
     ap.add_argument("--copies", action="store_true", help="host<->device copy times of the e2e buffers (not the benchmark line)")
     ap.add_argument("--rates", action="store_true", help="FP64 and FP32 GEMM rates of this GPU (not the benchmark line)")
+    ap.add_argument("--multi", action="store_true",
+                    help="12 point sources on 24^3x48: one multi-RHS solve against single solves (not the benchmark line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -610,6 +659,8 @@ def main():
         return run_copies(args)
     if args.rates:
         return run_rates(args)
+    if args.multi:
+        return run_multi(args)
 
     import torch
     rank, world, local = rank_info()
