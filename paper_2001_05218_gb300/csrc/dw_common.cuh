@@ -877,6 +877,10 @@ struct ColState {
   double gamma;    // |z|^2, z = A-side residual
   double alpha, beta;
   float alpha_f, beta_f;  // alpha and beta rounded to FP32 by the finalizer
+  // alpha of the iteration whose term alpha p is not yet in the low-precision
+  // increment xl (added by k_update_p or k_fold_x; 0 once added), and FP32
+  double alpha_x;
+  float alpha_xf;
   double rr;       // iterated |r|^2
   double rr_ref;   // |r|^2 at the last reliable update
   double bnorm2;   // |b|^2 (full lattice)
@@ -965,6 +969,8 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
       } else {
         C.alpha = C.gamma / v;
         C.alpha_f = (float)C.alpha;
+        C.alpha_x = C.alpha;
+        C.alpha_xf = C.alpha_f;
       }
       break;
     case FIN_UPDATE: {
@@ -998,6 +1004,8 @@ __device__ __forceinline__ void finalize(const RedArgs& ra, int col, double v) {
     case FIN_RELIABLE: {
       if (!C.do_rel) break;
       C.do_rel = 0;
+      C.alpha_x = 0.0;  // k_fold_x added alpha p to x
+      C.alpha_xf = 0.f;
       atomicSub(&ra.flags->rel_pending, 1);
       C.rr = v;
       C.rr_ref = v;

@@ -990,32 +990,24 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 // ------------------------------------------------------------------ site-local kernels
-// xl += alpha p;  r -= alpha w;  reduction |r|^2 -> FIN_UPDATE
-template <int SPL, int SPA>
-__global__ void __launch_bounds__(256) k_update_xr(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
+// r -= alpha w;  reduction |r|^2 -> FIN_UPDATE.  The matching x-increment
+// xl += alpha p is left to k_update_p (which reads p anyway) or, when a
+// reliable update comes first, to k_fold_x: ColState::alpha_x holds it.
+template <int SPL>
+__global__ void __launch_bounds__(256) k_update_r(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_ACTIVE)
   using RL = typename Spin<SPL>::R;
-  using RA = typename Spin<SPA>::R;
   typename RedT<RL>::type nrm = red_zero(typename RedT<RL>::type());
-  typename Spin<SPA>::Packed xlp;
   typename Spin<SPL>::Packed rp;
   if (valid) {
     const ColState& C = ra.cols[S.col0 + r];
-    Cx<RL> p[12], w[12], rv[12];
-    Cx<RA> xl[12];
-    Spin<SPL>::load(slot_ptr(S, S_P, r, par), S.vh, s, p);
+    Cx<RL> w[12], rv[12];
     Spin<SPL>::load(slot_ptr(S, S_W, r, par), S.vh, s, w);
     Spin<SPL>::load(slot_ptr(S, S_R, r, par), S.vh, s, rv);
-    Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
     const RL a = scalar_as<RL>(C.alpha, C.alpha_f);
-    const RA aa = scalar_as<RA>(C.alpha, C.alpha_f);
     RL n = (RL)0;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
-      xl[k] = cx(fma(aa, (RA)p[k].re, xl[k].re), fma(aa, (RA)p[k].im, xl[k].im));
-      rv[k] = cx(fma(-a, w[k].re, rv[k].re), fma(-a, w[k].im, rv[k].im));
-    }
-    xlp = Spin<SPA>::pack(xl);
+    for (int k = 0; k < 12; ++k) rv[k] = cx(fma(-a, w[k].re, rv[k].re), fma(-a, w[k].im, rv[k].im));
     // the norm is taken of the value as stored, so the recursion sees what
     // the next kernels will read
     Spin<SPL>::roundtrip(rv);
@@ -1026,23 +1018,31 @@ __global__ void __launch_bounds__(256) k_update_xr(const __grid_constant__ Batch
   }
   ra.fin = FIN_UPDATE;
   DW_BLOCK_REDUCE_STORE(nrm, [&] {
-    if (valid) {
-      Spin<SPA>::store_packed(slot_wptr(S, S_XL, r, par), S.vh, s, xlp);
-      Spin<SPL>::store_packed(slot_wptr(S, S_R, r, par), S.vh, s, rp);
-    }
+    if (valid) Spin<SPL>::store_packed(slot_wptr(S, S_R, r, par), S.vh, s, rp);
   })
 }
 
-// p = z + beta p
-template <int SPL>
+// xl += alpha_x p (the increment of the iteration that used p, unless a
+// reliable update has folded it already: alpha_x = 0);  p = z + beta p
+template <int SPL, int SPA>
 __global__ void __launch_bounds__(256) k_update_p(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_ACTIVE)
   if (valid) {
     using RL = typename Spin<SPL>::R;
-    const RL beta = scalar_as<RL>(ra.cols[S.col0 + r].beta, ra.cols[S.col0 + r].beta_f);
+    using RA = typename Spin<SPA>::R;
+    const ColState& C = ra.cols[S.col0 + r];
+    const RL beta = scalar_as<RL>(C.beta, C.beta_f);
     Cx<RL> p[12], z[12];
     Spin<SPL>::load(slot_ptr(S, S_P, r, par), S.vh, s, p);
     Spin<SPL>::load(slot_ptr(S, S_Z, r, par), S.vh, s, z);
+    if (C.alpha_x != 0.0) {
+      const RA aa = scalar_as<RA>(C.alpha_x, C.alpha_xf);
+      Cx<RA> xl[12];
+      Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) xl[k] = cx(fma(aa, (RA)p[k].re, xl[k].re), fma(aa, (RA)p[k].im, xl[k].im));
+      Spin<SPA>::store(slot_wptr(S, S_XL, r, par), S.vh, s, xl);
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) p[k] = cx(fma(beta, p[k].re, z[k].re), fma(beta, p[k].im, z[k].im));
     Spin<SPL>::store(slot_wptr(S, S_P, r, par), S.vh, s, p);
@@ -1069,17 +1069,29 @@ __global__ void __launch_bounds__(256) k_init_r(const __grid_constant__ Batch B,
   DW_BLOCK_REDUCE(nrm)
 }
 
-// x += xl; xl = 0 on the launched parities (start of a reliable update)
-template <int SPA, int SPH>
+// x += xl + alpha_x p; xl = 0 on the launched parities (start of a reliable
+// update: the pending increment of the current iteration is added first, in
+// the increment's precision, as k_update_p would have)
+template <int SPL, int SPA, int SPH>
 __global__ void __launch_bounds__(256) k_fold_x(const __grid_constant__ Batch B, int par_mode, RedArgs ra) {
   DW_BLOCK_PROLOGUE(G_REL)
   if (valid) {
+    using RL = typename Spin<SPL>::R;
     using RA = typename Spin<SPA>::R;
     using RH = typename Spin<SPH>::R;
+    const ColState& C = ra.cols[S.col0 + r];
     Cx<RH> x[12];
     Cx<RA> xl[12];
     Spin<SPH>::load(slot_ptr(S, S_X, r, par), S.vh, s, x);
     Spin<SPA>::load(slot_ptr(S, S_XL, r, par), S.vh, s, xl);
+    if (C.alpha_x != 0.0) {
+      const RA aa = scalar_as<RA>(C.alpha_x, C.alpha_xf);
+      Cx<RL> p[12];
+      Spin<SPL>::load(slot_ptr(S, S_P, r, par), S.vh, s, p);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) xl[k] = cx(fma(aa, (RA)p[k].re, xl[k].re), fma(aa, (RA)p[k].im, xl[k].im));
+      Spin<SPA>::roundtrip(xl);
+    }
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
       x[k] = cx(x[k].re + (RH)xl[k].re, x[k].im + (RH)xl[k].im);

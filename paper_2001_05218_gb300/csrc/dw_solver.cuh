@@ -74,7 +74,7 @@ struct CG {
     // (MODE_HERM: the same with the Laplacian's K)
     auto eo_reliable = [&] {
       count_launch();
-      k_fold_x<A, H><<<E.grid(0), E.P.block, 0, E.st>>>(E.P.B, 0, E.ra(FIN_STORE0));
+      k_fold_x<L, A, H><<<E.grid(0), E.P.block, 0, E.st>>>(E.P.B, 0, E.ra(FIN_STORE0));
       hop<H, H, false, false, OP>(E, 1, kLinkHi, InOne<H>{S_X}, EpiOut<H, C_ONE>{S_RT, G_REL});
       hop<H, H, false, false, OP>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiResidEO<L, H>{G_REL}, FIN_RELIABLE);
     };
@@ -84,12 +84,12 @@ struct CG {
       eo_reliable();
     } else if (mode == MODE_FULL) {
       count_launch();
-      k_fold_x<A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
+      k_fold_x<L, A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
       hop<H, H, false, false, OP>(E, 2, kLinkHi, InOne<H>{S_X}, EpiResidFull<L, true, H>{G_REL, S_RT, S_X, S_B},
                               FIN_RELIABLE);
     } else {
       count_launch();
-      k_fold_x<A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
+      k_fold_x<L, A, H><<<E.grid(2), E.P.block, 0, E.st>>>(E.P.B, 2, E.ra(FIN_STORE0));
       // t = D x ; r = b - D^dag t
       hop<H, H, false, false, OP>(E, 2, kLinkHi, InOne<H>{S_X}, EpiXpay<H, H, C_MK, false>{S_AUX0, S_X, G_REL});
       hop<H, H, false, true, OP>(E, 2, kLinkHi, InOne<H>{S_AUX0}, EpiResidFull<L, true, H>{G_REL, S_RT, S_AUX0, S_B},
@@ -192,7 +192,7 @@ dw_status CG<L, A, C12, H, OP>::build_graph(const Exec& E0, int mode, cudaGraphE
   wstep(E, mode);
   count_launch();
   count_launch();
-  k_update_xr<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_UPDATE));
+  k_update_r<L><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_UPDATE));
   finish(E, pm, FIN_UPDATE);
   k_cond_rel<<<1, 1, 0, E.st>>>(E.rb.flags, hr);
   {
@@ -220,7 +220,7 @@ dw_status CG<L, A, C12, H, OP>::build_graph(const Exec& E0, int mode, cudaGraphE
     c2 = pr.launches;
   }
   zstep(E, mode, FIN_BETA);
-  k_update_p<L><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_STORE0));
+  k_update_p<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_STORE0));
   k_cond_loop<<<1, 1, 0, E.st>>>(E.rb.flags, hw);
   count_launch();
   count_launch();
@@ -259,7 +259,7 @@ dw_status CG<L, A, C12, H, OP>::run_stepped(const Exec& E, int mode, int maxiter
     if (hf->active == 0) break;
     wstep(E, mode);
     count_launch();
-    k_update_xr<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_UPDATE));
+    k_update_r<L><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_UPDATE));
     finish(E, pm, FIN_UPDATE);
     DW_CUDA(cudaMemcpyAsync(hf, E.rb.flags, sizeof(Flags), cudaMemcpyDeviceToHost, E.st));
     DW_CUDA(cudaStreamSynchronize(E.st));
@@ -267,7 +267,7 @@ dw_status CG<L, A, C12, H, OP>::run_stepped(const Exec& E, int mode, int maxiter
     if (hf->active == 0) continue;
     zstep(E, mode, FIN_BETA);
     count_launch();
-    k_update_p<L><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_STORE0));
+    k_update_p<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_STORE0));
   }
   DW_CUDA(cudaGetLastError());
   return DW_OK;
@@ -450,7 +450,7 @@ dw_status CG<L, A, C12, H, OP>::run(const SolveArgs& a) {
   }
   zstep(E, mode, FIN_GAMMA0);  // z, gamma
   count_launch();
-  k_update_p<L><<<E.grid(eo ? 0 : 2), E.P.block, 0, st>>>(E.P.B, eo ? 0 : 2, E.ra(FIN_STORE0));  // p = z
+  k_update_p<L, A><<<E.grid(eo ? 0 : 2), E.P.block, 0, st>>>(E.P.B, eo ? 0 : 2, E.ra(FIN_STORE0));  // p = z
   DW_CUDA(cudaGetLastError());
 
   // ---- iterations
