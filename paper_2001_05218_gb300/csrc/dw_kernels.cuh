@@ -732,8 +732,15 @@ __device__ __forceinline__ void laplace_dirs(const SysDesc& S, const In& in, con
       Link<LP, C12>::load(lb, S.vh, li, u);
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        h0[k] = eta < 0.f ? cx(-p[k].re, -p[k].im) : p[k];
-        h1[k] = eta < 0.f ? cx(-p[6 + k].re, -p[6 + k].im) : p[6 + k];
+        h0[k] = p[k];
+        h1[k] = p[6 + k];
+      }
+      if (eta < 0.f) {  // boundary sign: taken only on the t-boundary slice
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          h0[k] = cx(-h0[k].re, -h0[k].im);
+          h1[k] = cx(-h1[k].re, -h1[k].im);
+        }
       }
       if (fwd) {
         su3_mul<false>(u, h0, g0);
@@ -742,10 +749,17 @@ __device__ __forceinline__ void laplace_dirs(const SysDesc& S, const In& in, con
         su3_mul<true>(u, h0, g0);
         su3_mul<true>(u, h1, g1);
       }
+      // double-float: sums left unnormalised, renormalised once after the
+      // eight directions (as the Wilson stencil's accumulation)
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        acc[k] = acc[k] + g0[k];
-        acc[6 + k] = acc[6 + k] + g1[k];
+        if constexpr (std::is_same<R, DF>::value) {
+          acc[k] = cadd_lazy(acc[k], g0[k]);
+          acc[6 + k] = cadd_lazy(acc[6 + k], g1[k]);
+        } else {
+          acc[k] = acc[k] + g0[k];
+          acc[6 + k] = acc[6 + k] + g1[k];
+        }
       }
     }
   }
