@@ -863,6 +863,7 @@ struct Batch {
   int RB;    // right-hand sides per block
   int ny;    // right-hand-side blocks, ceil(nrhs / RB): the grid is x = (parity
              // range, tile, rhs block) with the rhs block varying fastest
+  int rev;   // 1: blocks walk the grid from its end (see DW_BLOCK_PROLOGUE)
   SysDesc sd[kMaxSys];
 };
 

@@ -646,8 +646,9 @@ struct EpiResidFull {
   const int T = B.T, RB = B.RB;                                            \
   /* the right-hand-side block varies fastest: the blocks of one tile run  \
      together and share its links and neighbours in L2 */                  \
-  const int by = (int)(blockIdx.x % (unsigned)B.ny);                        \
-  int b = (int)(blockIdx.x / (unsigned)B.ny), par;                         \
+  const unsigned bx_ = B.rev ? gridDim.x - 1u - blockIdx.x : blockIdx.x;   \
+  const int by = (int)(bx_ % (unsigned)B.ny);                              \
+  int b = (int)(bx_ / (unsigned)B.ny), par;                                \
   if (par_mode == 2) {                                                     \
     par = b >= B.ntot ? 1 : 0;                                             \
     b -= par * B.ntot;                                                     \
@@ -915,8 +916,9 @@ __global__ void __launch_bounds__(256, 2)
   __shared__ int act[64];
   const int T = B.T, RB = B.RB;
   const unsigned ny = (unsigned)((B.sd[0].nrhs + 2 * RB - 1) / (2 * RB));
-  const int by = (int)(blockIdx.x % ny);
-  int b = (int)(blockIdx.x / ny), par;
+  const unsigned bx = B.rev ? gridDim.x - 1u - blockIdx.x : blockIdx.x;
+  const int by = (int)(bx % ny);
+  int b = (int)(bx / ny), par;
   if (par_mode == 2) {
     par = b >= B.ntot ? 1 : 0;
     b -= par * B.ntot;

@@ -102,7 +102,7 @@ struct CG {
     if constexpr (OP == OP_LAPLACE) {
       norm<L>(E, 0, S_R, fin);  // MODE_HERM: z aliases r
     } else if (mode == MODE_EO) {
-      hop<L, L, C12, true, OP>(E, 1, kLinkLo, InOne<L>{S_R}, EpiOut<L, C_ONE>{S_T, G_ACTIVE});
+      hop<L, L, C12, true, OP>(E.flipped(), 1, kLinkLo, InOne<L>{S_R}, EpiOut<L, C_ONE>{S_T, G_ACTIVE});
       hop<L, L, C12, true, OP>(E, 0, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK2, true>{S_Z, S_R, G_ACTIVE}, fin);
     } else if (mode == MODE_FULL) {
       hop<L, L, C12, true, OP>(E, 2, kLinkLo, InOne<L>{S_R}, EpiXpay<L, L, C_MK, true>{S_Z, S_R, G_ACTIVE}, fin);
@@ -118,7 +118,7 @@ struct CG {
       hop<L, L, C12, false, OP>(E, 0, kLinkLo, InOne<L>{S_T}, EpiXpayDot<L, L, C_MK2>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
     } else if (mode == MODE_EO) {
       hop<L, L, C12, false, OP>(E, 1, kLinkLo, InOne<L>{S_P}, EpiOut<L, C_ONE>{S_T, G_ACTIVE});
-      hop<L, L, C12, false, OP>(E, 0, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK2, true>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
+      hop<L, L, C12, false, OP>(E.flipped(), 0, kLinkLo, InOne<L>{S_T}, EpiXpay<L, L, C_MK2, true>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
     } else if (mode == MODE_FULL) {
       hop<L, L, C12, false, OP>(E, 2, kLinkLo, InOne<L>{S_P}, EpiXpay<L, L, C_MK, true>{S_W, S_P, G_ACTIVE}, FIN_ALPHA);
     } else {
@@ -220,7 +220,7 @@ dw_status CG<L, A, C12, H, OP>::build_graph(const Exec& E0, int mode, cudaGraphE
     c2 = pr.launches;
   }
   zstep(E, mode, FIN_BETA);
-  k_update_p<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_STORE0));
+  k_update_p<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.flipped().batch(), pm, E.ra(FIN_STORE0));
   k_cond_loop<<<1, 1, 0, E.st>>>(E.rb.flags, hw);
   count_launch();
   count_launch();
@@ -267,7 +267,7 @@ dw_status CG<L, A, C12, H, OP>::run_stepped(const Exec& E, int mode, int maxiter
     if (hf->active == 0) continue;
     zstep(E, mode, FIN_BETA);
     count_launch();
-    k_update_p<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.P.B, pm, E.ra(FIN_STORE0));
+    k_update_p<L, A><<<E.grid(pm), E.P.block, 0, E.st>>>(E.flipped().batch(), pm, E.ra(FIN_STORE0));
   }
   DW_CUDA(cudaGetLastError());
   return DW_OK;
