@@ -75,7 +75,9 @@ struct CG {
     auto eo_reliable = [&] {
       count_launch();
       k_fold_x<L, A, H><<<E.grid(0), E.P.block, 0, E.st>>>(E.P.B, 0, E.ra(FIN_STORE0));
-      hop<H, H, false, false, OP>(E, 1, kLinkHi, InOne<H>{S_X}, EpiOut<H, C_ONE>{S_RT, G_REL});
+      // grid directions alternate: fold forwards, H_oe backwards, H_eo forwards
+      // (the next stencil, z's first hop, walks backwards again)
+      hop<H, H, false, false, OP>(E.flipped(), 1, kLinkHi, InOne<H>{S_X}, EpiOut<H, C_ONE>{S_RT, G_REL});
       hop<H, H, false, false, OP>(E, 0, kLinkHi, InOne<H>{S_RT}, EpiResidEO<L, H>{G_REL}, FIN_RELIABLE);
     };
     if constexpr (OP == OP_LAPLACE) {
