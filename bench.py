@@ -834,10 +834,24 @@ def main():
         # the median over the steps is reported, the mean and every step beside it
         ne = max(5, args.steps)
         wall = []
+        # CUDA events around each step's two uploads (asynchronous: device time of
+        # the copies and layout kernels), beside the step's host clock
+        up_ev = []
         for _ in range(ne):
+            d = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
             a0 = time.perf_counter()
-            e2e_step()
+            d[0].record(stream)
+            dw.check(dw.dw_field_upload(Ug.handle, ctypes.c_void_p(Uh.data_ptr()), sp))
+            d[1].record(stream)
+            dw.check(dw.dw_field_upload(bg.handle, ctypes.c_void_p(bh.data_ptr()), sp))
+            d[2].record(stream)
+            reset_x()
+            dw.cg_solve(Ug, bg, xg, p_mix)
+            dw.check(dw.dw_field_download(xg.handle, ctypes.c_void_p(xh.data_ptr()), sp))
+            torch.cuda.current_stream().synchronize()
             wall.append(time.perf_counter() - a0)
+            up_ev.append(d)
+        torch.cuda.synchronize()
         barrier()
         # whole job: the slowest rank's median step, as for the device-timed value
         e2e_value, e2e_ms = aggregate_throughput(float(np.median(wall)) * 1e3, 1, world, "cuda")
@@ -865,7 +879,9 @@ def main():
         e2e = {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": int(Uh.numel() * 8 + bh.numel() * 8),
                "d2h_bytes_per_step": int(xh.numel() * 8), "ms_per_step": e2e_s * 1e3, "statistic": "median",
                "steps": ne, "mean_ms_per_step": float(np.mean(wall)) * 1e3,
-               "step_ms": [round(w * 1e3, 3) for w in wall], "phases_ms": phases}
+               "step_ms": [round(w * 1e3, 3) for w in wall],
+               "step_upload_ms": [[round(d[0].elapsed_time(d[1]), 3), round(d[1].elapsed_time(d[2]), 3)]
+                                  for d in up_ev], "phases_ms": phases}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
