@@ -473,6 +473,7 @@ def run_suite(args):
     MIX16 = dict(tol=1e-10, inner="f16", compress12=1, outer="df64", maxiter=100000)
     MIX32 = dict(tol=1e-10, inner="f32", outer="df64", maxiter=100000)
     MIXI16 = dict(tol=1e-10, inner="i16", compress12=1, outer="df64", maxiter=100000)
+    MIXB16 = dict(tol=1e-10, inner="bf16", compress12=1, outer="df64", maxiter=100000)
     if args.delta is not None:
         MIX16["delta"] = args.delta
     if args.delta32 is not None:
@@ -519,7 +520,8 @@ def run_suite(args):
     out["laplace_32x32x32x64_exp0.6"] = single_laplace("wilson_32x32x32x64_exp0.6", LAP[1:])
     out["wilson_32x32x32x64_exp0.6"] = single("wilson_32x32x32x64_exp0.6", [
         ("f16_mixed_eo", MIX16), ("f16_mixed_full_lattice", dict(MIX16, eo=0)),
-        ("f32_mixed_eo", MIX32), ("f32_mixed_12real_links", dict(MIX32, compress12=1)), ("i16_mixed_eo", MIXI16)])
+        ("f32_mixed_eo", MIX32), ("f32_mixed_12real_links", dict(MIX32, compress12=1)), ("i16_mixed_eo", MIXI16),
+        ("bf16_mixed_eo", MIXB16)])
     # 12 point sources on 24^3x48: one multi-RHS solve vs 12 single solves
     name = "wilson_24x24x24x48_exp0.4_12src"
     dims, kappa, U, _ = I.make_workload(name, with_source=False)
